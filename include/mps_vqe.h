@@ -1,0 +1,195 @@
+/*
+ * mps_vqe.h - C-ABI of the GB300 (sm_103a) MPS circuit simulator and
+ * Pauli-sum energy of arXiv:2303.03681 ("Towards practical and massively
+ * parallel quantum computing emulation for quantum chemistry").
+ *
+ * The library (libmpsvqe.so) keeps a matrix product state in right-canonical
+ * form on one GPU and applies one- and two-qubit gates to it with the
+ * Hastings update and SVD truncation (Methods, "MPS algorithm for quantum
+ * circuit simulation": Eqs. mps, rightcanonicalcondition, tildeC, svdtildeC,
+ * Bl), and evaluates E = sum_k c_k <psi|P_k|psi> over Pauli strings by
+ * Eqs. expec1/expec2 (Methods, "The implementation of UCCSD with matrix
+ * produce states"), sharing left environments between strings with a common
+ * prefix.
+ *
+ * Conventions (all calls):
+ *  - Sites are qubits 0..n-1.  Site tensor B_n has shape
+ *    [chi_{n-1}][2][chi_n] (row-major).  Bond b sits left of site b
+ *    (b = 0..n, chi_0 = chi_n = 1) and carries the singular values lam_b.
+ *  - A two-qubit gate acts on adjacent sites (q, q+1); its 4x4 matrix is
+ *    indexed by 2*i_q + i_{q+1} (site q is the more significant bit).  A
+ *    statevector index has qubit 0 as its most significant bit.
+ *  - Complex numbers in host arrays are (re, im) pairs of doubles.
+ *  - Host arrays passed in are read during the call and stay owned by the
+ *    caller.  Handles are owned by the library until the matching *_destroy.
+ *  - Every call returns an mps_status and never aborts the process; the
+ *    message of the last failure on the calling thread is mps_last_error().
+ *  - Work is issued on the context's CUDA stream.  Calls that return host
+ *    results synchronise that stream; calls named *_async do not.
+ *  - Calls on one context are not thread-safe; different contexts are.
+ */
+#ifndef MPS_VQE_H
+#define MPS_VQE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MPS_OK = 0,
+  MPS_EINVAL = 1,     /* bad argument (null handle, non-adjacent gate, size) */
+  MPS_ENOMEM = 2,     /* device allocation failed or the allocation cap was hit */
+  MPS_ECUDA = 3,      /* a CUDA runtime call failed */
+  MPS_ETIMEOUT = 4,   /* a bounded device-side wait ran out */
+  MPS_ENOTCONV = 5,   /* the Jacobi SVD hit its sweep cap (result still written) */
+  MPS_EBUSY = 6,      /* serving queue full */
+  MPS_ESTATE = 7      /* state left inconsistent by an earlier failure: reset it */
+} mps_status;
+
+/* Arithmetic of a state.  The truncation SVD and the energy sum are FP64 in
+ * every mode unless mps_config.svd_fp64 = 0. */
+typedef enum {
+  MPS_PREC_FP64 = 0,  /* complex128 storage, FP64 contractions */
+  MPS_PREC_FP32 = 1   /* complex64 storage, FP32 contractions */
+} mps_precision;
+
+typedef struct {
+  int32_t chi_max;        /* bond-dimension cap (>= 1) */
+  int32_t precision;      /* mps_precision */
+  double trunc_rel;       /* keep s_i > trunc_rel * s_1 (0: keep all nonzero) */
+  int32_t svd_fp64;       /* 1: FP64 Jacobi SVD; 0: SVD in the storage precision */
+  int32_t svd_max_sweeps; /* Jacobi sweep cap; 0 selects 60 */
+  double svd_tol;         /* rotate a pair while |b_ij| > tol sqrt(b_ii b_jj); 0: default */
+} mps_config;
+
+/* One gate.  arity 1: u holds the 2x2 matrix (4 complex = 8 doubles, row
+ * major); arity 2: the 4x4 matrix (16 complex = 32 doubles).  A two-qubit
+ * gate acts on (q, q+1) and needs q + 1 < n. */
+typedef struct {
+  int32_t q;
+  int32_t arity;
+  double u[32];
+} mps_gate;
+
+/* One gate of a circuit template: G = exp(i phi) M_plus + exp(-i phi) M_minus
+ * with phi = coeff * theta[param]; param = -1 marks a fixed gate (G = M_plus
+ * + M_minus).  Matrix layout as in mps_gate. */
+typedef struct {
+  int32_t q;
+  int32_t arity;
+  int32_t param;
+  int32_t reserved;
+  double coeff;
+  double m_plus[32];
+  double m_minus[32];
+} mps_template_gate;
+
+/* Truncation statistics accumulated since the last reset. */
+typedef struct {
+  double discarded_weight;  /* sum over gates of 1 - sum(kept s^2) / sum(s^2) */
+  double min_kept_sv;       /* smallest kept normalised singular value */
+  int32_t max_chi;          /* largest bond dimension reached */
+  int32_t degenerate_cuts;  /* cuts at chi_max inside a pair equal to 1e-10 */
+  int32_t svd_not_converged;/* SVDs that hit the sweep cap */
+  int32_t max_sweeps_used;  /* largest number of Jacobi sweeps of one SVD */
+  int64_t two_qubit_gates;  /* two-qubit gates applied */
+} mps_report;
+
+typedef struct mps_ctx mps_ctx;
+typedef struct mps_state mps_state;
+typedef struct mps_ham mps_ham;
+typedef struct mps_circuit mps_circuit;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* mps_last_error(void);
+
+/* Library version string. */
+const char* mps_version(void);
+
+/* Create a context on CUDA device `device` issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = a new non-blocking stream owned by the context). */
+mps_status mps_ctx_create(int device, void* cuda_stream, mps_ctx** out);
+mps_status mps_ctx_synchronize(mps_ctx* ctx);
+/* Cap on the device bytes this context may allocate (0 = no cap).  An
+ * allocation beyond it fails with MPS_ENOMEM. */
+mps_status mps_ctx_set_alloc_limit(mps_ctx* ctx, size_t bytes);
+mps_status mps_ctx_bytes_allocated(const mps_ctx* ctx, size_t* out);
+void mps_ctx_destroy(mps_ctx* ctx);
+
+/* Create an n-qubit MPS in the computational basis state |init_bits>
+ * (init_bits: n bytes, 0/1; NULL = |0...0>) - the chi = 1 product state of
+ * the paper's Hartree-Fock reference.  Device memory for every site is sized
+ * for min(chi_max, 2^b, 2^(n-b)) on each bond. */
+mps_status mps_create(mps_ctx* ctx, int32_t n_qubits, const uint8_t* init_bits,
+                      const mps_config* cfg, mps_state** out);
+/* Return the state to |init_bits> (NULL = |0...0>) and clear its report. */
+mps_status mps_reset(mps_state* st, const uint8_t* init_bits);
+void mps_destroy(mps_state* st);
+
+/* Apply n gates in order (one-qubit: Methods single-qubit gate equation;
+ * two-qubit: Hastings update of Eqs. tildeC, svdtildeC, Bl with truncation
+ * to min(chi_max, #{s_i > trunc_rel s_1}) and renormalisation of the kept
+ * singular values).  `report` (nullable) receives the accumulated
+ * statistics; this call synchronises the stream. */
+mps_status mps_apply_gates(mps_state* st, const mps_gate* gates, size_t n, mps_report* report);
+
+/* Upload a circuit template (see mps_template_gate) with n_params angles. */
+mps_status mps_circuit_create(mps_ctx* ctx, int32_t n_qubits, const mps_template_gate* gates,
+                              size_t n_gates, int32_t n_params, mps_circuit** out);
+void mps_circuit_destroy(mps_circuit* c);
+/* Bind theta (host array of n_params doubles, or a device pointer when
+ * theta_on_device != 0) and apply the circuit without synchronising. */
+mps_status mps_apply_circuit_async(mps_state* st, const mps_circuit* c, const double* theta,
+                                   int theta_on_device);
+
+/* Upload a Hamiltonian sum_k coeffs[k] P_k: ops is n_terms x n_qubits bytes
+ * (0=I 1=X 2=Y 3=Z), coeffs real.  The strings are arranged on the host in
+ * a prefix trie (first non-identity site, then the operators left to right)
+ * whose nodes are the shared left environments of Eq. expec2. */
+mps_status mps_hamiltonian_create(mps_ctx* ctx, int32_t n_qubits, size_t n_terms,
+                                  const uint8_t* ops, const double* coeffs, mps_ham** out);
+/* Trie statistics: n_nodes materialised environments, n_levels sites. */
+mps_status mps_hamiltonian_info(const mps_ham* h, int64_t* n_terms, int64_t* n_nodes,
+                                int64_t* max_level_nodes);
+void mps_ham_destroy(mps_ham* h);
+
+/* E = sum_k c_k <P_k> in FP64 (Eq. expec2 per string: lam^2 of the bond left
+ * of the first non-identity site, transfer products to the last one, trace);
+ * norm_out (nullable) gets sum(lam_1^2) of the first bond.  Synchronises. */
+mps_status mps_energy(mps_state* st, const mps_ham* h, double* energy_out, double* norm_out);
+/* Same, writing the energy to device memory without synchronising. */
+mps_status mps_energy_async(mps_state* st, const mps_ham* h, double* d_energy_out);
+/* Per-term expectation values <P_k> (host array of n_terms doubles). */
+mps_status mps_expectations(mps_state* st, const mps_ham* h, double* values_out);
+
+/* Bond dimensions chi_0..chi_n (host array of n+1 int32). */
+mps_status mps_bond_dims(mps_state* st, int32_t* chi_out);
+/* Host copy of the state: tensors_out receives every B_n (row-major
+ * [chi_{n-1}][2][chi_n], complex128 as (re, im)) back to back; lam_out every
+ * lam_b, b = 0..n, back to back.  Sizes follow mps_bond_dims. */
+mps_status mps_export(mps_state* st, double* tensors_out, size_t tensors_cap_doubles, double* lam_out,
+                      size_t lam_cap);
+mps_status mps_get_report(mps_state* st, mps_report* out);
+
+/* One VQE energy evaluation per request: reset to init_bits, apply the
+ * template bound to theta, evaluate the Hamiltonian.  Requests run in order
+ * on the context stream; energies_out[i] (host) and status_out[i]
+ * (nullable) receive the results.  theta and init_bits are host arrays. */
+typedef struct {
+  mps_state* state;
+  const mps_circuit* circuit;
+  const mps_ham* ham;
+  const double* theta;
+  const uint8_t* init_bits;
+} vqe_request;
+mps_status vqe_eval(mps_ctx* ctx, const vqe_request* reqs, size_t n, double* energies_out,
+                    mps_status* status_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPS_VQE_H */

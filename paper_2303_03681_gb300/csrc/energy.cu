@@ -1,0 +1,381 @@
+// Hamiltonian upload (prefix trie of the Pauli strings) and the Pauli-sum
+// energy of Eq. expec2 with shared left environments.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+
+#include "gate_kernels.cuh"
+#include "energy_kernels.cuh"
+#include "internal.h"
+
+namespace mpsv {
+
+namespace {
+
+struct Node {
+  int level;   // site of the last operator; -1 for a start node
+  int parent;  // node id; start nodes have -1
+  int op;
+  int slot = -1;   // environment slot at its level (nodes with children)
+  int entry = -1;  // parent-entry index at the next level (nodes with children, start nodes)
+  bool has_child = false;
+  std::vector<int> terms;
+};
+
+}  // namespace
+
+// Builds the trie on the host.  Start node s (id s < n) stands for diag(lam_s^2)
+// on the bond left of site s; node (parent, op) extends its parent's string by
+// one site.
+static mps_status build_trie(mps_ham* h, const uint8_t* ops, const double* coeffs, std::vector<int>& parent_src,
+                             std::vector<int2>& child, std::vector<int4>& leaf, std::vector<int2>& trace) {
+  const int n = h->n;
+  std::vector<Node> nodes(n);
+  for (int s = 0; s < n; ++s) {
+    nodes[s].level = -1;
+    nodes[s].parent = -1;
+    nodes[s].op = 0;
+  }
+  std::unordered_map<uint64_t, int> edge;
+  edge.reserve(1 << 16);
+  for (long long t = 0; t < h->n_terms; ++t) {
+    const uint8_t* row = ops + (size_t)t * n;
+    int first = -1, last = -1;
+    for (int j = 0; j < n; ++j) {
+      if (row[j] > 3) {
+        set_error("mps_hamiltonian_create: ops[%lld, %d] = %d is not in 0..3", t, j, (int)row[j]);
+        return MPS_EINVAL;
+      }
+      if (row[j]) {
+        if (first < 0) first = j;
+        last = j;
+      }
+    }
+    if (!std::isfinite(coeffs[t])) {
+      set_error("mps_hamiltonian_create: coefficient %lld is not finite", t);
+      return MPS_EINVAL;
+    }
+    if (first < 0) continue;  // identity: <I> = 1 (vals prefilled)
+    int cur = first;
+    for (int j = first; j <= last; ++j) {
+      const uint64_t key = ((uint64_t)cur << 2) | row[j];
+      auto it = edge.find(key);
+      int nxt;
+      if (it == edge.end()) {
+        nxt = (int)nodes.size();
+        Node nd;
+        nd.level = j;
+        nd.parent = cur;
+        nd.op = row[j];
+        nodes.push_back(nd);
+        edge.emplace(key, nxt);
+      } else {
+        nxt = it->second;
+      }
+      nodes[cur].has_child = true;
+      cur = nxt;
+    }
+    nodes[cur].terms.push_back((int)t);
+  }
+  // bucket real nodes by level (creation order inside a level)
+  std::vector<std::vector<int>> by_level(n);
+  for (size_t id = n; id < nodes.size(); ++id) by_level[nodes[id].level].push_back((int)id);
+  h->levels.assign(n, LevelHost());
+  long long n_mat = 0, max_level = 0;
+  for (int j = 0; j < n; ++j) {
+    LevelHost& L = h->levels[j];
+    L.off_parent = parent_src.size();
+    L.off_child = child.size();
+    L.off_leaf = leaf.size();
+    L.off_trace = trace.size();
+    int n_entries = 0;
+    int slots = 0;
+    for (int id : by_level[j]) {
+      Node& nd = nodes[id];
+      Node& par = nodes[nd.parent];
+      if (par.entry < 0) {
+        par.entry = n_entries++;
+        parent_src.push_back(par.level < 0 ? -1 : par.slot);
+      }
+      if (nd.has_child) {
+        nd.slot = slots++;
+        child.push_back(make_int2(par.entry, nd.op));
+      }
+    }
+    for (int id : by_level[j]) {
+      const Node& nd = nodes[id];
+      for (int t : nd.terms) {
+        if (nd.has_child)
+          trace.push_back(make_int2(nd.slot, t));
+        else
+          leaf.push_back(make_int4(nodes[nd.parent].entry, nd.op, t, 0));
+      }
+    }
+    L.n_parents = n_entries;
+    L.n_children = slots;
+    L.n_leaves = (int)(leaf.size() - L.off_leaf);
+    L.n_traces = (int)(trace.size() - L.off_trace);
+    n_mat += slots;
+    max_level = std::max<long long>(max_level, slots);
+  }
+  h->n_nodes = n_mat;
+  h->max_level_nodes = max_level;
+  return MPS_OK;
+}
+
+template <typename R>
+static mps_status ensure_env_buffers(mps_state* st, mps_ham* h) {
+  size_t Lneed = 16, Mneed = 16;
+  for (int j = 0; j < h->n; ++j) {
+    const LevelHost& L = h->levels[j];
+    const size_t cl = st->cap[j], cr = st->cap[j + 1];
+    Lneed = std::max(Lneed, (size_t)L.n_children * cr * cr * sizeof(cplx<R>));
+    Mneed = std::max(Mneed, (size_t)L.n_parents * 2 * cl * cr * sizeof(cplx<R>));
+  }
+  mps_ctx* c = h->ctx;
+  if (Lneed > h->L_bytes) {
+    dev_free(c, h->d_L[0]);
+    dev_free(c, h->d_L[1]);
+    h->d_L[0] = h->d_L[1] = nullptr;
+    h->L_bytes = 0;
+    mps_status rc = dev_alloc(c, &h->d_L[0], Lneed);
+    if (rc == MPS_OK) rc = dev_alloc(c, &h->d_L[1], Lneed);
+    if (rc != MPS_OK) return rc;
+    h->L_bytes = Lneed;
+  }
+  if (Mneed > h->M_bytes) {
+    dev_free(c, h->d_M);
+    h->d_M = nullptr;
+    h->M_bytes = 0;
+    mps_status rc = dev_alloc(c, &h->d_M, Mneed);
+    if (rc != MPS_OK) return rc;
+    h->M_bytes = Mneed;
+  }
+  return MPS_OK;
+}
+
+template <typename R>
+static mps_status energy_levels(mps_state* st, mps_ham* h, double* d_out) {
+  mps_status rc = ensure_env_buffers<R>(st, h);
+  if (rc != MPS_OK) return rc;
+  cudaStream_t s = st->ctx->stream;
+  const long long nt = h->n_terms;
+  if (nt) fill_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(h->d_vals, nt, 1.0);
+  const cplx<R>* B = reinterpret_cast<const cplx<R>*>(st->d_B);
+  cplx<R>* Lprev = reinterpret_cast<cplx<R>*>(h->d_L[0]);
+  cplx<R>* Lcur = reinterpret_cast<cplx<R>*>(h->d_L[1]);
+  cplx<R>* M = reinterpret_cast<cplx<R>*>(h->d_M);
+  const dim3 blk(kTile, kTile);
+  for (int j = 0; j < h->n; ++j) {
+    const LevelHost& L = h->levels[j];
+    if (!L.n_parents) continue;
+    EnvLevel lv;
+    lv.parent_src = h->d_parent_src + L.off_parent;
+    lv.child = h->d_child + L.off_child;
+    lv.leaf = h->d_leaf + L.off_leaf;
+    lv.trace = h->d_trace + L.off_trace;
+    lv.n_parents = L.n_parents;
+    lv.n_children = L.n_children;
+    lv.n_leaves = L.n_leaves;
+    lv.n_traces = L.n_traces;
+    lv.site = j;
+    lv.cap_l = st->cap[j];
+    lv.cap_r = st->cap[j + 1];
+    const cplx<R>* Bj = B + st->site_off[j];
+    const int tl = (lv.cap_l + kTile - 1) / kTile, tr = (lv.cap_r + kTile - 1) / kTile;
+    env_m_kernel<R><<<(unsigned)((size_t)L.n_parents * tl * tr), blk, 0, s>>>(
+        Lprev, Bj, st->d_lam + st->lam_off[j], st->d_chi, lv, M);
+    if (L.n_children)
+      env_child_kernel<R><<<(unsigned)((size_t)L.n_children * tr * tr), blk, 0, s>>>(M, Bj, st->d_chi, lv, Lcur);
+    if (L.n_leaves) env_leaf_kernel<R><<<(L.n_leaves + 7) / 8, 256, 0, s>>>(M, Bj, st->d_chi, lv, h->d_vals);
+    if (L.n_traces) env_trace_kernel<R><<<(L.n_traces + 7) / 8, 256, 0, s>>>(Lcur, st->d_chi, lv, h->d_vals);
+    if (L.n_children) std::swap(Lprev, Lcur);
+  }
+  energy_reduce_kernel<<<1, 1024, 0, s>>>(h->d_vals, h->d_coeffs, nt, 0.0, d_out);
+  MPSV_CUDA(cudaGetLastError());
+  return MPS_OK;
+}
+
+mps_status ham_energy_async(mps_state* st, mps_ham* h, double* d_out) {
+  if (h->n != st->n || h->ctx != st->ctx) {
+    set_error("energy: Hamiltonian on %d qubits / another context, state has %d", h->n, st->n);
+    return MPS_EINVAL;
+  }
+  if (st->broken) {
+    set_error("energy: state is inconsistent after an earlier failure; reset it");
+    return MPS_ESTATE;
+  }
+  return st->fp32 ? energy_levels<float>(st, h, d_out) : energy_levels<double>(st, h, d_out);
+}
+
+static void destroy_ham(mps_ham* h) {
+  if (!h) return;
+  mps_ctx* c = h->ctx;
+  DeviceGuard guard(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (void* p : {(void*)h->d_parent_src, (void*)h->d_child, (void*)h->d_leaf, (void*)h->d_trace,
+                  (void*)h->d_coeffs, (void*)h->d_vals, (void*)h->d_energy, h->d_L[0], h->d_L[1], h->d_M})
+    dev_free(c, p);
+  delete h;
+}
+
+}  // namespace mpsv
+
+using namespace mpsv;
+
+extern "C" {
+
+mps_status mps_hamiltonian_create(mps_ctx* ctx, int32_t n_qubits, size_t n_terms, const uint8_t* ops,
+                                  const double* coeffs, mps_ham** out) {
+  if (!ctx || !out || (n_terms && (!ops || !coeffs))) {
+    set_error("mps_hamiltonian_create: NULL argument");
+    return MPS_EINVAL;
+  }
+  *out = nullptr;
+  if (n_qubits < 2 || n_terms > (size_t)INT32_MAX) {
+    set_error("mps_hamiltonian_create: n_qubits = %d, n_terms = %zu", n_qubits, n_terms);
+    return MPS_EINVAL;
+  }
+  auto* h = new mps_ham();
+  h->ctx = ctx;
+  h->n = n_qubits;
+  h->n_terms = (long long)n_terms;
+  std::vector<int> parent_src;
+  std::vector<int2> child;
+  std::vector<int4> leaf;
+  std::vector<int2> trace;
+  mps_status rc = build_trie(h, ops, coeffs, parent_src, child, leaf, trace);
+  if (rc != MPS_OK) {
+    delete h;
+    return rc;
+  }
+  DeviceGuard guard(ctx->device);
+  auto up = [&](void** dst, const void* src, size_t bytes) {
+    if (rc != MPS_OK) return;
+    rc = dev_alloc(ctx, dst, std::max<size_t>(bytes, 16));
+    if (rc == MPS_OK && bytes) {
+      cudaError_t e = cudaMemcpyAsync(*dst, src, bytes, cudaMemcpyHostToDevice, ctx->stream);
+      if (e != cudaSuccess) rc = cuda_fail(e, "mps_hamiltonian_create upload");
+    }
+  };
+  up((void**)&h->d_parent_src, parent_src.data(), parent_src.size() * sizeof(int));
+  up((void**)&h->d_child, child.data(), child.size() * sizeof(int2));
+  up((void**)&h->d_leaf, leaf.data(), leaf.size() * sizeof(int4));
+  up((void**)&h->d_trace, trace.data(), trace.size() * sizeof(int2));
+  up((void**)&h->d_coeffs, coeffs, n_terms * sizeof(double));
+  if (rc == MPS_OK) rc = dev_alloc(ctx, (void**)&h->d_vals, std::max<size_t>(16, n_terms * sizeof(double)));
+  if (rc == MPS_OK) rc = dev_alloc(ctx, (void**)&h->d_energy, sizeof(double));
+  if (rc == MPS_OK) {
+    cudaError_t e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "mps_hamiltonian_create");
+  }
+  if (rc != MPS_OK) {
+    destroy_ham(h);
+    return rc;
+  }
+  *out = h;
+  return MPS_OK;
+}
+
+mps_status mps_hamiltonian_info(const mps_ham* h, int64_t* n_terms, int64_t* n_nodes, int64_t* max_level_nodes) {
+  if (!h) {
+    set_error("mps_hamiltonian_info: NULL Hamiltonian");
+    return MPS_EINVAL;
+  }
+  if (n_terms) *n_terms = h->n_terms;
+  if (n_nodes) *n_nodes = h->n_nodes;
+  if (max_level_nodes) *max_level_nodes = h->max_level_nodes;
+  return MPS_OK;
+}
+
+void mps_ham_destroy(mps_ham* h) { destroy_ham(h); }
+
+mps_status mps_energy_async(mps_state* st, const mps_ham* h, double* d_energy_out) {
+  if (!st || !h || !d_energy_out) {
+    set_error("mps_energy_async: NULL argument");
+    return MPS_EINVAL;
+  }
+  DeviceGuard guard(st->ctx->device);
+  return ham_energy_async(st, const_cast<mps_ham*>(h), d_energy_out);
+}
+
+mps_status mps_energy(mps_state* st, const mps_ham* h, double* energy_out, double* norm_out) {
+  if (!st || !h || !energy_out) {
+    set_error("mps_energy: NULL argument");
+    return MPS_EINVAL;
+  }
+  DeviceGuard guard(st->ctx->device);
+  mps_ham* hh = const_cast<mps_ham*>(h);
+  mps_status rc = ham_energy_async(st, hh, hh->d_energy);
+  if (rc != MPS_OK) return rc;
+  MPSV_CUDA(cudaMemcpyAsync(energy_out, hh->d_energy, sizeof(double), cudaMemcpyDeviceToHost, st->ctx->stream));
+  if (norm_out) {
+    // sum of lam^2 on bond 1 (the first inner bond; bond 0 is the trivial edge)
+    const int b = st->n > 1 ? 1 : 0;
+    std::vector<int> chi(st->n + 1);
+    MPSV_CUDA(cudaMemcpyAsync(chi.data(), st->d_chi, (st->n + 1) * sizeof(int), cudaMemcpyDeviceToHost,
+                              st->ctx->stream));
+    MPSV_CUDA(cudaStreamSynchronize(st->ctx->stream));
+    std::vector<double> lam(chi[b]);
+    MPSV_CUDA(cudaMemcpyAsync(lam.data(), st->d_lam + st->lam_off[b], chi[b] * sizeof(double),
+                              cudaMemcpyDeviceToHost, st->ctx->stream));
+    MPSV_CUDA(cudaStreamSynchronize(st->ctx->stream));
+    double s = 0.0;
+    for (double v : lam) s += v * v;
+    *norm_out = s;
+  }
+  MPSV_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  return MPS_OK;
+}
+
+mps_status mps_expectations(mps_state* st, const mps_ham* h, double* values_out) {
+  if (!st || !h || (!values_out && h->n_terms)) {
+    set_error("mps_expectations: NULL argument");
+    return MPS_EINVAL;
+  }
+  DeviceGuard guard(st->ctx->device);
+  mps_ham* hh = const_cast<mps_ham*>(h);
+  mps_status rc = ham_energy_async(st, hh, hh->d_energy);
+  if (rc != MPS_OK) return rc;
+  if (h->n_terms)
+    MPSV_CUDA(cudaMemcpyAsync(values_out, hh->d_vals, h->n_terms * sizeof(double), cudaMemcpyDeviceToHost,
+                              st->ctx->stream));
+  MPSV_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  return MPS_OK;
+}
+
+mps_status vqe_eval(mps_ctx* ctx, const vqe_request* reqs, size_t n, double* energies_out,
+                    mps_status* status_out) {
+  if (!ctx || (n && (!reqs || !energies_out))) {
+    set_error("vqe_eval: NULL argument");
+    return MPS_EINVAL;
+  }
+  DeviceGuard guard(ctx->device);
+  mps_status first_bad = MPS_OK;
+  for (size_t i = 0; i < n; ++i) {
+    const vqe_request& r = reqs[i];
+    mps_status rc = MPS_OK;
+    if (!r.state || !r.circuit || !r.ham || r.state->ctx != ctx) {
+      set_error("vqe_eval: request %zu has a NULL handle or another context", i);
+      rc = MPS_EINVAL;
+    }
+    if (rc == MPS_OK) rc = state_reset(r.state, r.init_bits);
+    if (rc == MPS_OK) rc = mps_apply_circuit_async(r.state, r.circuit, r.theta, 0);
+    if (rc == MPS_OK) rc = ham_energy_async(r.state, const_cast<mps_ham*>(r.ham), r.ham->d_energy);
+    if (rc == MPS_OK) {
+      cudaError_t e = cudaMemcpyAsync(&energies_out[i], r.ham->d_energy, sizeof(double), cudaMemcpyDeviceToHost,
+                                      ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) rc = cuda_fail(e, "vqe_eval");
+    }
+    if (rc != MPS_OK) {
+      energies_out[i] = 0.0;
+      if (first_bad == MPS_OK) first_bad = rc;
+    }
+    if (status_out) status_out[i] = rc;
+  }
+  return first_bad;
+}
+
+}  // extern "C"

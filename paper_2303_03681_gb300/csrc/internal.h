@@ -1,0 +1,126 @@
+// Host-side objects behind the opaque handles of mps_vqe.h.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/mps_vqe.h"
+#include "common.cuh"
+
+namespace mpsv {
+
+void set_error(const char* fmt, ...);
+mps_status cuda_fail(cudaError_t e, const char* what);
+
+#define MPSV_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace mpsv
+
+struct mps_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  size_t alloc_limit = 0;
+  size_t allocated = 0;
+  std::map<void*, size_t> allocs;
+};
+
+namespace mpsv {
+mps_status dev_alloc(mps_ctx* ctx, void** p, size_t bytes);
+void dev_free(mps_ctx* ctx, void* p);
+}  // namespace mpsv
+
+struct mps_state {
+  mps_ctx* ctx = nullptr;
+  int n = 0;
+  mps_config cfg{};
+  bool fp32 = false;   // complex64 storage
+  bool svd64 = true;   // FP64 Jacobi
+  std::vector<int> cap;          // bond capacities, n + 1
+  std::vector<size_t> site_off;  // complex elements
+  std::vector<size_t> lam_off;   // doubles
+  void* d_B = nullptr;
+  double* d_lam = nullptr;
+  int* d_chi = nullptr;
+  size_t* d_site_off = nullptr;
+  size_t* d_lam_off = nullptr;
+  uint8_t* d_bits = nullptr;
+  mpsv::DevReport* d_rep = nullptr;
+  void* d_C = nullptr;  // theta C, m x n (storage precision)
+  void* d_A = nullptr;  // SVD matrix, m x n (SVD precision)
+  void* d_V = nullptr;  // n x n (SVD precision)
+  mpsv::DevGate* d_gates = nullptr;
+  size_t gates_cap = 0;
+  size_t total_lam = 0;
+  size_t total_elems = 0;
+  std::vector<uint8_t> last_bits;
+  bool broken = false;
+};
+
+struct mps_circuit {
+  mps_ctx* ctx = nullptr;
+  int n = 0;
+  int n_params = 0;
+  int n_gates = 0;
+  std::vector<int> q, arity;
+  mpsv::DevTmplGate* d_tmpl = nullptr;
+  mpsv::DevGate* d_bound = nullptr;
+  double* d_theta = nullptr;
+};
+
+namespace mpsv {
+struct LevelHost {
+  int n_parents = 0, n_children = 0, n_leaves = 0, n_traces = 0;
+  size_t off_parent = 0, off_child = 0, off_leaf = 0, off_trace = 0;
+};
+}  // namespace mpsv
+
+struct mps_ham {
+  mps_ctx* ctx = nullptr;
+  int n = 0;
+  long long n_terms = 0;
+  long long n_nodes = 0;
+  long long max_level_nodes = 0;
+  std::vector<mpsv::LevelHost> levels;
+  int* d_parent_src = nullptr;
+  int2* d_child = nullptr;
+  int4* d_leaf = nullptr;
+  int2* d_trace = nullptr;
+  double* d_coeffs = nullptr;
+  double* d_vals = nullptr;
+  double* d_energy = nullptr;
+  // environment buffers (sized for the largest state seen)
+  void* d_L[2] = {nullptr, nullptr};
+  void* d_M = nullptr;
+  size_t L_bytes = 0, M_bytes = 0;
+};
+
+namespace mpsv {
+// state.cu
+mps_status state_apply_device_gates(mps_state* st, const DevGate* d_gates, const int* q, const int* arity, size_t n);
+mps_status state_reset(mps_state* st, const uint8_t* bits);
+// energy.cu
+mps_status ham_energy_async(mps_state* st, mps_ham* h, double* d_out);
+}  // namespace mpsv

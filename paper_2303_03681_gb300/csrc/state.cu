@@ -1,0 +1,622 @@
+// Contexts, states, gates and circuit templates of libmpsvqe.
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+
+#include "gate_kernels.cuh"
+#include "internal.h"
+
+namespace mpsv {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+const char* last_error() { return g_last_error.c_str(); }
+
+mps_status cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? MPS_ENOMEM : MPS_ECUDA;
+}
+
+mps_status dev_alloc(mps_ctx* ctx, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) bytes = 16;
+  if (ctx->alloc_limit && ctx->allocated + bytes > ctx->alloc_limit) {
+    set_error("allocation of %zu bytes exceeds the context cap (%zu of %zu in use)", bytes, ctx->allocated,
+              ctx->alloc_limit);
+    return MPS_ENOMEM;
+  }
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    set_error("cudaMalloc(%zu): %s", bytes, cudaGetErrorString(e));
+    return MPS_ENOMEM;
+  }
+  ctx->allocated += bytes;
+  ctx->allocs[*p] = bytes;
+  return MPS_OK;
+}
+
+void dev_free(mps_ctx* ctx, void* p) {
+  if (!p) return;
+  auto it = ctx->allocs.find(p);
+  if (it != ctx->allocs.end()) {
+    ctx->allocated -= it->second;
+    ctx->allocs.erase(it);
+  }
+  cudaFree(p);
+}
+
+static int bond_cap(int b, int n, int chi_max) {
+  int e = std::min(b, n - b);
+  if (e >= 30) return chi_max;
+  return std::min(chi_max, 1 << e);
+}
+
+// ---------------------------------------------------------------------------
+// kernel launch helpers
+// ---------------------------------------------------------------------------
+template <typename R> static cplx<R>* site_ptr(mps_state* st, int s) {
+  return reinterpret_cast<cplx<R>*>(st->d_B) + st->site_off[s];
+}
+
+template <typename S> static size_t svd_smem_bytes(int mcap, int ncap, bool use_smem) {
+  size_t b = (size_t)ncap * (sizeof(double) + sizeof(int)) + 64;
+  if (use_smem) b += ((size_t)mcap * ncap + (size_t)ncap * ncap) * sizeof(cplx<S>);
+  return b;
+}
+
+static size_t max_dyn_smem() {
+  static size_t v = 0;
+  static std::once_flag f;
+  std::call_once(f, [] {
+    int dev = 0, val = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&val, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    v = (size_t)val;
+  });
+  return v;
+}
+
+template <typename S, typename R> static void svd_set_attr() {
+  static std::once_flag f;
+  std::call_once(f, [] {
+    cudaFuncSetAttribute(svd_truncate_kernel<S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(max_dyn_smem() - 1024));
+  });
+}
+
+template <typename R, typename S>
+static void launch_two_qubit(mps_state* st, const DevGate* g, int q, cudaStream_t s) {
+  const int cap_l = st->cap[q], cap_m = st->cap[q + 1], cap_r = st->cap[q + 2];
+  const dim3 blk(kTile, kTile);
+  const dim3 g1((cap_r + kTile - 1) / kTile, (cap_l + kTile - 1) / kTile);
+  theta_kernel<R, S><<<g1, blk, 0, s>>>(site_ptr<R>(st, q), site_ptr<R>(st, q + 1), g, st->d_lam + st->lam_off[q],
+                                        st->d_chi, q, reinterpret_cast<cplx<R>*>(st->d_C),
+                                        reinterpret_cast<cplx<S>*>(st->d_A));
+  const int mcap = 2 * cap_l, ncap = 2 * cap_r;
+  const size_t full = svd_smem_bytes<S>(mcap, ncap, true);
+  const bool use_smem = full + 2048 <= max_dyn_smem();
+  const size_t smem = svd_smem_bytes<S>(mcap, ncap, use_smem);
+  svd_set_attr<S, R>();
+  int warps = std::min(32, std::max(1, ncap / 2));
+  SvdParams p;
+  p.chi_max = st->cfg.chi_max;
+  p.max_sweeps = st->cfg.svd_max_sweeps > 0 ? st->cfg.svd_max_sweeps : 60;
+  p.trunc_rel = st->cfg.trunc_rel;
+  p.tol = st->cfg.svd_tol;
+  svd_truncate_kernel<S, R><<<1, 32 * warps, smem, s>>>(
+      reinterpret_cast<cplx<S>*>(st->d_A), reinterpret_cast<cplx<S>*>(st->d_V), use_smem ? 1 : 0, st->d_chi, q, p,
+      site_ptr<R>(st, q + 1), st->d_lam + st->lam_off[q + 1], st->d_rep);
+  const dim3 g3((cap_m + kTile - 1) / kTile, (2 * cap_l + kTile - 1) / kTile);
+  g3_kernel<R><<<g3, blk, 0, s>>>(reinterpret_cast<cplx<R>*>(st->d_C), site_ptr<R>(st, q + 1), st->d_chi, q,
+                                  st->d_rep, site_ptr<R>(st, q));
+}
+
+template <typename R>
+static void launch_one_qubit(mps_state* st, const DevGate* g, int q, cudaStream_t s) {
+  const int tot = st->cap[q] * st->cap[q + 1];
+  gate1_kernel<R><<<(tot + 255) / 256, 256, 0, s>>>(site_ptr<R>(st, q), g, st->d_chi, q);
+}
+
+mps_status state_apply_device_gates(mps_state* st, const DevGate* d_gates, const int* q, const int* arity,
+                                    size_t n) {
+  cudaStream_t s = st->ctx->stream;
+  for (size_t i = 0; i < n; ++i) {
+    const DevGate* g = d_gates + i;
+    if (arity[i] == 1) {
+      if (st->fp32)
+        launch_one_qubit<float>(st, g, q[i], s);
+      else
+        launch_one_qubit<double>(st, g, q[i], s);
+    } else {
+      if (st->fp32) {
+        if (st->svd64)
+          launch_two_qubit<float, double>(st, g, q[i], s);
+        else
+          launch_two_qubit<float, float>(st, g, q[i], s);
+      } else {
+        if (st->svd64)
+          launch_two_qubit<double, double>(st, g, q[i], s);
+        else
+          launch_two_qubit<double, float>(st, g, q[i], s);
+      }
+    }
+  }
+  MPSV_CUDA(cudaGetLastError());
+  return MPS_OK;
+}
+
+mps_status state_reset(mps_state* st, const uint8_t* bits) {
+  cudaStream_t s = st->ctx->stream;
+  std::vector<uint8_t> hb(st->n, 0);
+  if (bits) {
+    for (int i = 0; i < st->n; ++i) {
+      if (bits[i] > 1) {
+        set_error("init_bits[%d] = %d is not 0 or 1", i, (int)bits[i]);
+        return MPS_EINVAL;
+      }
+      hb[i] = bits[i];
+    }
+  }
+  if (hb != st->last_bits) {
+    MPSV_CUDA(cudaMemcpyAsync(st->d_bits, hb.data(), st->n, cudaMemcpyHostToDevice, s));
+    MPSV_CUDA(cudaStreamSynchronize(s));  // hb is a stack copy
+    st->last_bits = hb;
+  }
+  const int threads = 256, blocks = (st->n + 1 + threads - 1) / threads;
+  if (st->fp32)
+    reset_kernel<float><<<blocks, threads, 0, s>>>(reinterpret_cast<float2*>(st->d_B), st->d_site_off, st->d_lam,
+                                                   st->d_lam_off, st->d_chi, st->d_bits, st->n, st->d_rep);
+  else
+    reset_kernel<double><<<blocks, threads, 0, s>>>(reinterpret_cast<double2*>(st->d_B), st->d_site_off, st->d_lam,
+                                                    st->d_lam_off, st->d_chi, st->d_bits, st->n, st->d_rep);
+  MPSV_CUDA(cudaGetLastError());
+  st->broken = false;
+  return MPS_OK;
+}
+
+static void destroy_state(mps_state* st) {
+  if (!st) return;
+  mps_ctx* c = st->ctx;
+  DeviceGuard guard(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (void* p : {st->d_B, (void*)st->d_lam, (void*)st->d_chi, (void*)st->d_site_off, (void*)st->d_lam_off,
+                  (void*)st->d_bits, (void*)st->d_rep, st->d_C, st->d_A, st->d_V, (void*)st->d_gates})
+    dev_free(c, p);
+  delete st;
+}
+
+static void host_gate_to_dev(const mps_gate& g, DevGate& d) {
+  std::memset(&d, 0, sizeof(d));
+  d.q = g.q;
+  d.arity = g.arity;
+  const int cnt = g.arity == 1 ? 4 : 16;
+  for (int e = 0; e < cnt; ++e) d.u[e] = make_double2(g.u[2 * e], g.u[2 * e + 1]);
+}
+
+}  // namespace mpsv
+
+using namespace mpsv;
+
+extern "C" {
+
+const char* mps_last_error(void) { return mpsv::last_error(); }
+
+const char* mps_version(void) { return "libmpsvqe 0.1.0 (sm_103a)"; }
+
+mps_status mps_ctx_create(int device, void* cuda_stream, mps_ctx** out) {
+  if (!out) {
+    set_error("mps_ctx_create: out is NULL");
+    return MPS_EINVAL;
+  }
+  *out = nullptr;
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    set_error("mps_ctx_create: no CUDA device %d (%d visible%s%s)", device, count, e != cudaSuccess ? ", " : "",
+              e != cudaSuccess ? cudaGetErrorString(e) : "");
+    return e != cudaSuccess ? MPS_ECUDA : MPS_EINVAL;
+  }
+  DeviceGuard guard(device);
+  auto* c = new mps_ctx();
+  c->device = device;
+  if (cuda_stream) {
+    c->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      delete c;
+      return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    c->own_stream = true;
+  }
+  *out = c;
+  return MPS_OK;
+}
+
+mps_status mps_ctx_synchronize(mps_ctx* ctx) {
+  if (!ctx) {
+    set_error("mps_ctx_synchronize: NULL context");
+    return MPS_EINVAL;
+  }
+  DeviceGuard guard(ctx->device);
+  MPSV_CUDA(cudaStreamSynchronize(ctx->stream));
+  return MPS_OK;
+}
+
+mps_status mps_ctx_set_alloc_limit(mps_ctx* ctx, size_t bytes) {
+  if (!ctx) {
+    set_error("mps_ctx_set_alloc_limit: NULL context");
+    return MPS_EINVAL;
+  }
+  ctx->alloc_limit = bytes;
+  return MPS_OK;
+}
+
+mps_status mps_ctx_bytes_allocated(const mps_ctx* ctx, size_t* out) {
+  if (!ctx || !out) {
+    set_error("mps_ctx_bytes_allocated: NULL argument");
+    return MPS_EINVAL;
+  }
+  *out = ctx->allocated;
+  return MPS_OK;
+}
+
+void mps_ctx_destroy(mps_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard guard(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->allocs) cudaFree(kv.first);
+  ctx->allocs.clear();
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+mps_status mps_create(mps_ctx* ctx, int32_t n_qubits, const uint8_t* init_bits, const mps_config* cfg,
+                      mps_state** out) {
+  if (!ctx || !cfg || !out) {
+    set_error("mps_create: NULL argument");
+    return MPS_EINVAL;
+  }
+  *out = nullptr;
+  if (n_qubits < 2 || n_qubits > 100000) {
+    set_error("mps_create: n_qubits = %d outside [2, 100000]", n_qubits);
+    return MPS_EINVAL;
+  }
+  if (cfg->chi_max < 1 || cfg->chi_max > 1024) {
+    set_error("mps_create: chi_max = %d outside [1, 1024]", cfg->chi_max);
+    return MPS_EINVAL;
+  }
+  if (cfg->precision != MPS_PREC_FP64 && cfg->precision != MPS_PREC_FP32) {
+    set_error("mps_create: unknown precision %d", cfg->precision);
+    return MPS_EINVAL;
+  }
+  if (!(cfg->trunc_rel >= 0.0 && cfg->trunc_rel < 1.0)) {
+    set_error("mps_create: trunc_rel = %g outside [0, 1)", cfg->trunc_rel);
+    return MPS_EINVAL;
+  }
+  DeviceGuard guard(ctx->device);
+  auto* st = new mps_state();
+  st->ctx = ctx;
+  st->n = n_qubits;
+  st->cfg = *cfg;
+  st->fp32 = cfg->precision == MPS_PREC_FP32;
+  st->svd64 = cfg->svd_fp64 != 0;
+  const int n = n_qubits;
+  st->cap.resize(n + 1);
+  for (int b = 0; b <= n; ++b) st->cap[b] = bond_cap(b, n, cfg->chi_max);
+  st->site_off.resize(n);
+  st->lam_off.resize(n + 1);
+  size_t off = 0, loff = 0;
+  size_t max_mn = 1, max_nn = 1;
+  for (int s = 0; s < n; ++s) {
+    st->site_off[s] = off;
+    off += (size_t)st->cap[s] * 2 * st->cap[s + 1];
+  }
+  for (int b = 0; b <= n; ++b) {
+    st->lam_off[b] = loff;
+    loff += st->cap[b];
+  }
+  for (int q = 0; q + 1 < n; ++q) {
+    const size_t m = 2 * (size_t)st->cap[q], nn = 2 * (size_t)st->cap[q + 2];
+    max_mn = std::max(max_mn, m * nn);
+    max_nn = std::max(max_nn, nn * nn);
+  }
+  st->total_elems = off;
+  st->total_lam = loff;
+  const size_t celem = st->fp32 ? sizeof(float2) : sizeof(double2);
+  const size_t selem = st->svd64 ? sizeof(double2) : sizeof(float2);
+  mps_status rc = MPS_OK;
+  auto A = [&](void** p, size_t bytes) {
+    if (rc == MPS_OK) rc = dev_alloc(ctx, p, bytes);
+  };
+  A(&st->d_B, off * celem);
+  A((void**)&st->d_lam, loff * sizeof(double));
+  A((void**)&st->d_chi, (n + 1) * sizeof(int));
+  A((void**)&st->d_site_off, n * sizeof(size_t));
+  A((void**)&st->d_lam_off, (n + 1) * sizeof(size_t));
+  A((void**)&st->d_bits, n);
+  A((void**)&st->d_rep, sizeof(DevReport));
+  A(&st->d_C, max_mn * celem);
+  A(&st->d_A, max_mn * selem);
+  A(&st->d_V, max_nn * selem);
+  if (rc != MPS_OK) {
+    destroy_state(st);
+    return rc;
+  }
+  cudaStream_t s = ctx->stream;
+  cudaError_t e = cudaMemcpyAsync(st->d_site_off, st->site_off.data(), n * sizeof(size_t),
+                                  cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(st->d_lam_off, st->lam_off.data(), (n + 1) * sizeof(size_t), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st->d_B, 0, off * celem, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st->d_lam, 0, loff * sizeof(double), s);
+  if (e != cudaSuccess) {
+    destroy_state(st);
+    return cuda_fail(e, "mps_create upload");
+  }
+  rc = state_reset(st, init_bits);
+  if (rc != MPS_OK) {
+    destroy_state(st);
+    return rc;
+  }
+  *out = st;
+  return MPS_OK;
+}
+
+mps_status mps_reset(mps_state* st, const uint8_t* init_bits) {
+  if (!st) {
+    set_error("mps_reset: NULL state");
+    return MPS_EINVAL;
+  }
+  DeviceGuard guard(st->ctx->device);
+  return state_reset(st, init_bits);
+}
+
+void mps_destroy(mps_state* st) { destroy_state(st); }
+
+mps_status mps_get_report(mps_state* st, mps_report* out) {
+  if (!st || !out) {
+    set_error("mps_get_report: NULL argument");
+    return MPS_EINVAL;
+  }
+  DeviceGuard guard(st->ctx->device);
+  DevReport r;
+  MPSV_CUDA(cudaMemcpyAsync(&r, st->d_rep, sizeof(r), cudaMemcpyDeviceToHost, st->ctx->stream));
+  MPSV_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  out->discarded_weight = r.discarded_weight;
+  out->min_kept_sv = r.min_kept_sv;
+  out->max_chi = r.max_chi;
+  out->degenerate_cuts = r.degenerate_cuts;
+  out->svd_not_converged = r.not_converged;
+  out->max_sweeps_used = r.max_sweeps;
+  out->two_qubit_gates = r.two_qubit_gates;
+  return MPS_OK;
+}
+
+mps_status mps_apply_gates(mps_state* st, const mps_gate* gates, size_t n, mps_report* report) {
+  if (!st || (!gates && n)) {
+    set_error("mps_apply_gates: NULL argument");
+    return MPS_EINVAL;
+  }
+  if (st->broken) {
+    set_error("mps_apply_gates: state is inconsistent after an earlier failure; reset it");
+    return MPS_ESTATE;
+  }
+  std::vector<int> q(n), ar(n);
+  std::vector<DevGate> hg(n);
+  for (size_t i = 0; i < n; ++i) {
+    const mps_gate& g = gates[i];
+    if (g.arity != 1 && g.arity != 2) {
+      set_error("mps_apply_gates: gate %zu has arity %d", i, g.arity);
+      return MPS_EINVAL;
+    }
+    if (g.q < 0 || g.q + g.arity > st->n) {
+      set_error("mps_apply_gates: gate %zu on site %d (arity %d) outside 0..%d", i, g.q, g.arity, st->n - 1);
+      return MPS_EINVAL;
+    }
+    q[i] = g.q;
+    ar[i] = g.arity;
+    host_gate_to_dev(g, hg[i]);
+  }
+  DeviceGuard guard(st->ctx->device);
+  if (n > st->gates_cap) {
+    dev_free(st->ctx, st->d_gates);
+    st->d_gates = nullptr;
+    st->gates_cap = 0;
+    mps_status rc = dev_alloc(st->ctx, (void**)&st->d_gates, n * sizeof(DevGate));
+    if (rc != MPS_OK) return rc;
+    st->gates_cap = n;
+  }
+  if (n) {
+    MPSV_CUDA(cudaMemcpyAsync(st->d_gates, hg.data(), n * sizeof(DevGate), cudaMemcpyHostToDevice,
+                              st->ctx->stream));
+    mps_status rc = state_apply_device_gates(st, st->d_gates, q.data(), ar.data(), n);
+    if (rc != MPS_OK) {
+      st->broken = true;
+      return rc;
+    }
+  }
+  cudaError_t e = cudaStreamSynchronize(st->ctx->stream);
+  if (e != cudaSuccess) {
+    st->broken = true;
+    return cuda_fail(e, "mps_apply_gates");
+  }
+  if (report) return mps_get_report(st, report);
+  return MPS_OK;
+}
+
+mps_status mps_bond_dims(mps_state* st, int32_t* chi_out) {
+  if (!st || !chi_out) {
+    set_error("mps_bond_dims: NULL argument");
+    return MPS_EINVAL;
+  }
+  DeviceGuard guard(st->ctx->device);
+  MPSV_CUDA(cudaMemcpyAsync(chi_out, st->d_chi, (st->n + 1) * sizeof(int), cudaMemcpyDeviceToHost,
+                            st->ctx->stream));
+  MPSV_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  return MPS_OK;
+}
+
+mps_status mps_export(mps_state* st, double* tensors_out, size_t tensors_cap_doubles, double* lam_out,
+                      size_t lam_cap) {
+  if (!st || !tensors_out || !lam_out) {
+    set_error("mps_export: NULL argument");
+    return MPS_EINVAL;
+  }
+  DeviceGuard guard(st->ctx->device);
+  std::vector<int> chi(st->n + 1);
+  mps_status rc = mps_bond_dims(st, chi.data());
+  if (rc != MPS_OK) return rc;
+  size_t need = 0, need_lam = 0;
+  for (int s = 0; s < st->n; ++s) need += 2 * (size_t)chi[s] * 2 * chi[s + 1];
+  for (int b = 0; b <= st->n; ++b) need_lam += chi[b];
+  if (need > tensors_cap_doubles || need_lam > lam_cap) {
+    set_error("mps_export: buffers too small (need %zu tensor doubles, %zu lam doubles)", need, need_lam);
+    return MPS_EINVAL;
+  }
+  const size_t celem = st->fp32 ? sizeof(float2) : sizeof(double2);
+  std::vector<unsigned char> raw(st->total_elems * celem);
+  std::vector<double> lam(st->total_lam);
+  MPSV_CUDA(cudaMemcpyAsync(raw.data(), st->d_B, raw.size(), cudaMemcpyDeviceToHost, st->ctx->stream));
+  MPSV_CUDA(cudaMemcpyAsync(lam.data(), st->d_lam, lam.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                            st->ctx->stream));
+  MPSV_CUDA(cudaStreamSynchronize(st->ctx->stream));
+  size_t o = 0;
+  for (int s = 0; s < st->n; ++s) {
+    const size_t cnt = (size_t)chi[s] * 2 * chi[s + 1];
+    for (size_t e = 0; e < cnt; ++e) {
+      if (st->fp32) {
+        const float2 z = reinterpret_cast<const float2*>(raw.data())[st->site_off[s] + e];
+        tensors_out[o++] = z.x;
+        tensors_out[o++] = z.y;
+      } else {
+        const double2 z = reinterpret_cast<const double2*>(raw.data())[st->site_off[s] + e];
+        tensors_out[o++] = z.x;
+        tensors_out[o++] = z.y;
+      }
+    }
+  }
+  o = 0;
+  for (int b = 0; b <= st->n; ++b)
+    for (int a = 0; a < chi[b]; ++a) lam_out[o++] = lam[st->lam_off[b] + a];
+  return MPS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// circuit templates
+// ---------------------------------------------------------------------------
+mps_status mps_circuit_create(mps_ctx* ctx, int32_t n_qubits, const mps_template_gate* gates, size_t n_gates,
+                              int32_t n_params, mps_circuit** out) {
+  if (!ctx || !out || (!gates && n_gates)) {
+    set_error("mps_circuit_create: NULL argument");
+    return MPS_EINVAL;
+  }
+  *out = nullptr;
+  if (n_params < 0 || n_qubits < 2) {
+    set_error("mps_circuit_create: n_qubits = %d, n_params = %d", n_qubits, n_params);
+    return MPS_EINVAL;
+  }
+  std::vector<DevTmplGate> ht(n_gates);
+  auto* c = new mps_circuit();
+  c->ctx = ctx;
+  c->n = n_qubits;
+  c->n_params = n_params;
+  c->n_gates = (int)n_gates;
+  c->q.resize(n_gates);
+  c->arity.resize(n_gates);
+  for (size_t i = 0; i < n_gates; ++i) {
+    const mps_template_gate& g = gates[i];
+    if ((g.arity != 1 && g.arity != 2) || g.q < 0 || g.q + g.arity > n_qubits || g.param >= n_params) {
+      set_error("mps_circuit_create: gate %zu invalid (q=%d arity=%d param=%d)", i, g.q, g.arity, g.param);
+      delete c;
+      return MPS_EINVAL;
+    }
+    DevTmplGate& d = ht[i];
+    std::memset(&d, 0, sizeof(d));
+    d.q = g.q;
+    d.arity = g.arity;
+    d.param = g.param < 0 ? -1 : g.param;
+    d.coeff = g.coeff;
+    const int cnt = g.arity == 1 ? 4 : 16;
+    for (int e = 0; e < cnt; ++e) {
+      d.mp[e] = make_double2(g.m_plus[2 * e], g.m_plus[2 * e + 1]);
+      d.mm[e] = make_double2(g.m_minus[2 * e], g.m_minus[2 * e + 1]);
+    }
+    c->q[i] = g.q;
+    c->arity[i] = g.arity;
+  }
+  DeviceGuard guard(ctx->device);
+  mps_status rc = dev_alloc(ctx, (void**)&c->d_tmpl, std::max<size_t>(1, n_gates) * sizeof(DevTmplGate));
+  if (rc == MPS_OK) rc = dev_alloc(ctx, (void**)&c->d_bound, std::max<size_t>(1, n_gates) * sizeof(DevGate));
+  if (rc == MPS_OK) rc = dev_alloc(ctx, (void**)&c->d_theta, std::max(1, n_params) * sizeof(double));
+  if (rc == MPS_OK && n_gates) {
+    cudaError_t e = cudaMemcpyAsync(c->d_tmpl, ht.data(), n_gates * sizeof(DevTmplGate), cudaMemcpyHostToDevice,
+                                    ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) rc = cuda_fail(e, "mps_circuit_create upload");
+  }
+  if (rc != MPS_OK) {
+    dev_free(ctx, c->d_tmpl);
+    dev_free(ctx, c->d_bound);
+    dev_free(ctx, c->d_theta);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return MPS_OK;
+}
+
+void mps_circuit_destroy(mps_circuit* c) {
+  if (!c) return;
+  DeviceGuard guard(c->ctx->device);
+  cudaStreamSynchronize(c->ctx->stream);
+  dev_free(c->ctx, c->d_tmpl);
+  dev_free(c->ctx, c->d_bound);
+  dev_free(c->ctx, c->d_theta);
+  delete c;
+}
+
+mps_status mps_apply_circuit_async(mps_state* st, const mps_circuit* c, const double* theta, int theta_on_device) {
+  if (!st || !c || (!theta && c->n_params)) {
+    set_error("mps_apply_circuit_async: NULL argument");
+    return MPS_EINVAL;
+  }
+  if (c->n != st->n || c->ctx != st->ctx) {
+    set_error("mps_apply_circuit_async: circuit for %d qubits / another context, state has %d", c->n, st->n);
+    return MPS_EINVAL;
+  }
+  if (st->broken) {
+    set_error("mps_apply_circuit_async: state is inconsistent after an earlier failure; reset it");
+    return MPS_ESTATE;
+  }
+  DeviceGuard guard(st->ctx->device);
+  cudaStream_t s = st->ctx->stream;
+  const double* d_theta = theta;
+  if (!theta_on_device && c->n_params) {
+    MPSV_CUDA(cudaMemcpyAsync(c->d_theta, theta, c->n_params * sizeof(double), cudaMemcpyHostToDevice, s));
+    d_theta = c->d_theta;
+  }
+  if (c->n_gates) {
+    bind_kernel<<<c->n_gates, 32, 0, s>>>(c->d_tmpl, c->n_gates, d_theta ? d_theta : c->d_theta, c->d_bound);
+    mps_status rc = state_apply_device_gates(st, c->d_bound, c->q.data(), c->arity.data(), c->n_gates);
+    if (rc != MPS_OK) {
+      st->broken = true;
+      return rc;
+    }
+  }
+  return MPS_OK;
+}
+
+}  // extern "C"

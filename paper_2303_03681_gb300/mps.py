@@ -1,0 +1,356 @@
+"""Python binding of the C-ABI in include/mps_vqe.h (argument marshalling only).
+
+Every operation runs in libmpsvqe.so on the GPU; there is no Python or CPU
+fallback.  Importing this module loads the library and raises if it is
+missing or cannot be loaded.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmpsvqe.so")
+
+MPS_OK, MPS_EINVAL, MPS_ENOMEM, MPS_ECUDA, MPS_ETIMEOUT, MPS_ENOTCONV, MPS_EBUSY, MPS_ESTATE = range(8)
+STATUS_NAMES = ["MPS_OK", "MPS_EINVAL", "MPS_ENOMEM", "MPS_ECUDA", "MPS_ETIMEOUT", "MPS_ENOTCONV", "MPS_EBUSY",
+                "MPS_ESTATE"]
+PRECISIONS = {"fp64": 0, "fp32": 1}
+
+# numpy views of the C structs (layouts match include/mps_vqe.h on LP64 hosts)
+GATE_DTYPE = np.dtype([("q", "<i4"), ("arity", "<i4"), ("u", "<f8", (32,))])
+TEMPLATE_GATE_DTYPE = np.dtype([("q", "<i4"), ("arity", "<i4"), ("param", "<i4"), ("reserved", "<i4"),
+                                ("coeff", "<f8"), ("m_plus", "<f8", (32,)), ("m_minus", "<f8", (32,))])
+assert GATE_DTYPE.itemsize == 264 and TEMPLATE_GATE_DTYPE.itemsize == 536
+
+
+class MpsError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {message}")
+        self.status = status
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("chi_max", ctypes.c_int32), ("precision", ctypes.c_int32), ("trunc_rel", ctypes.c_double),
+                ("svd_fp64", ctypes.c_int32), ("svd_max_sweeps", ctypes.c_int32), ("svd_tol", ctypes.c_double)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("discarded_weight", ctypes.c_double), ("min_kept_sv", ctypes.c_double),
+                ("max_chi", ctypes.c_int32), ("degenerate_cuts", ctypes.c_int32),
+                ("svd_not_converged", ctypes.c_int32), ("max_sweeps_used", ctypes.c_int32),
+                ("two_qubit_gates", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class VqeRequest(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_void_p), ("circuit", ctypes.c_void_p), ("ham", ctypes.c_void_p),
+                ("theta", ctypes.c_void_p), ("init_bits", ctypes.c_void_p)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; "
+                           f"g.build()\"` (needs nvcc for sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, SZ, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t, ctypes.c_double
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "mps_last_error": ([], ctypes.c_char_p),
+        "mps_version": ([], ctypes.c_char_p),
+        "mps_ctx_create": ([ctypes.c_int, P, PP], ctypes.c_int),
+        "mps_ctx_synchronize": ([P], ctypes.c_int),
+        "mps_ctx_set_alloc_limit": ([P, SZ], ctypes.c_int),
+        "mps_ctx_bytes_allocated": ([P, ctypes.POINTER(SZ)], ctypes.c_int),
+        "mps_ctx_destroy": ([P], None),
+        "mps_create": ([P, I32, P, ctypes.POINTER(Config), PP], ctypes.c_int),
+        "mps_reset": ([P, P], ctypes.c_int),
+        "mps_destroy": ([P], None),
+        "mps_apply_gates": ([P, P, SZ, ctypes.POINTER(Report)], ctypes.c_int),
+        "mps_circuit_create": ([P, I32, P, SZ, I32, PP], ctypes.c_int),
+        "mps_circuit_destroy": ([P], None),
+        "mps_apply_circuit_async": ([P, P, P, ctypes.c_int], ctypes.c_int),
+        "mps_hamiltonian_create": ([P, I32, SZ, P, P, PP], ctypes.c_int),
+        "mps_hamiltonian_info": ([P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+        "mps_ham_destroy": ([P], None),
+        "mps_energy": ([P, P, ctypes.POINTER(D), ctypes.POINTER(D)], ctypes.c_int),
+        "mps_energy_async": ([P, P, P], ctypes.c_int),
+        "mps_expectations": ([P, P, P], ctypes.c_int),
+        "mps_bond_dims": ([P, P], ctypes.c_int),
+        "mps_export": ([P, P, SZ, P, SZ], ctypes.c_int),
+        "mps_get_report": ([P, ctypes.POINTER(Report)], ctypes.c_int),
+        "vqe_eval": ([P, P, SZ, P, P], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = _load()
+
+
+def library():
+    return _lib
+
+
+def _check(status):
+    if status != MPS_OK:
+        raise MpsError(status, _lib.mps_last_error().decode())
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+def version() -> str:
+    return _lib.mps_version().decode()
+
+
+# ---------------------------------------------------------------------------
+# marshalling of generator objects
+# ---------------------------------------------------------------------------
+
+def _pack_matrices(u, arity):
+    """(G, 4, 4) complex -> (G, 32) doubles: 4x4 row-major, or 2x2 first."""
+    g = u.shape[0]
+    out = np.zeros((g, 32))
+    two = arity == 2
+    m4 = np.ascontiguousarray(u[two]).reshape(-1, 16)
+    out[two] = np.stack([m4.real, m4.imag], axis=-1).reshape(-1, 32)
+    m2 = np.ascontiguousarray(u[~two][:, :2, :2]).reshape(-1, 4)
+    out[~two, :8] = np.stack([m2.real, m2.imag], axis=-1).reshape(-1, 8)
+    return out
+
+
+def gates_to_abi(gates) -> np.ndarray:
+    """GateList -> array of mps_gate."""
+    arr = np.zeros(gates.n_gates, dtype=GATE_DTYPE)
+    arr["q"] = gates.q
+    arr["arity"] = gates.arity
+    arr["u"] = _pack_matrices(np.asarray(gates.u), np.asarray(gates.arity))
+    return arr
+
+
+def template_to_abi(tmpl) -> np.ndarray:
+    """CircuitTemplate -> array of mps_template_gate."""
+    arr = np.zeros(tmpl.n_gates, dtype=TEMPLATE_GATE_DTYPE)
+    arr["q"] = tmpl.q
+    arr["arity"] = tmpl.arity
+    arr["param"] = tmpl.param
+    arr["coeff"] = tmpl.coeff
+    arr["m_plus"] = _pack_matrices(tmpl.m_plus, tmpl.arity)
+    arr["m_minus"] = _pack_matrices(tmpl.m_minus, tmpl.arity)
+    return arr
+
+
+# ---------------------------------------------------------------------------
+# handles
+# ---------------------------------------------------------------------------
+
+class Context:
+    """A device and the CUDA stream the library issues its work on.
+
+    ``stream`` may be a torch.cuda.Stream, an integer cudaStream_t or None (a
+    private non-blocking stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        handle = ctypes.c_void_p()
+        s = None
+        if stream is not None:
+            s = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        _check(_lib.mps_ctx_create(int(device), s, ctypes.byref(handle)))
+        self.handle = handle
+        self.device = device
+        self._stream = stream
+
+    def synchronize(self):
+        _check(_lib.mps_ctx_synchronize(self.handle))
+
+    def set_alloc_limit(self, nbytes: int):
+        _check(_lib.mps_ctx_set_alloc_limit(self.handle, int(nbytes)))
+
+    def bytes_allocated(self) -> int:
+        v = ctypes.c_size_t()
+        _check(_lib.mps_ctx_bytes_allocated(self.handle, ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if self.handle:
+            _lib.mps_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hamiltonian:
+    def __init__(self, ctx: Context, ham):
+        self.ctx = ctx
+        self.n_qubits = int(ham.n_qubits)
+        ops = np.ascontiguousarray(ham.ops, dtype=np.uint8)
+        coeffs = np.ascontiguousarray(ham.coeffs, dtype=np.float64)
+        self.n_terms = int(ops.shape[0])
+        h = ctypes.c_void_p()
+        _check(_lib.mps_hamiltonian_create(ctx.handle, self.n_qubits, self.n_terms, _ptr(ops), _ptr(coeffs),
+                                           ctypes.byref(h)))
+        self.handle = h
+
+    def info(self):
+        a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.mps_hamiltonian_info(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return {"n_terms": a.value, "n_nodes": b.value, "max_level_nodes": c.value}
+
+    def close(self):
+        if self.handle:
+            _lib.mps_ham_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Circuit:
+    def __init__(self, ctx: Context, tmpl):
+        self.ctx = ctx
+        self.n_qubits = int(tmpl.n_qubits)
+        self.n_params = int(tmpl.n_params)
+        self.n_gates = int(tmpl.n_gates)
+        arr = template_to_abi(tmpl)
+        h = ctypes.c_void_p()
+        _check(_lib.mps_circuit_create(ctx.handle, self.n_qubits, _ptr(arr), arr.shape[0], self.n_params,
+                                       ctypes.byref(h)))
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            _lib.mps_circuit_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class State:
+    """A right-canonical MPS on the GPU."""
+
+    def __init__(self, ctx: Context, n_qubits: int, init_bits=None, chi_max: int = 64, precision: str = "fp64",
+                 trunc_rel: float = 0.0, svd_fp64: bool = True, svd_max_sweeps: int = 0, svd_tol: float = 0.0):
+        self.ctx = ctx
+        self.n = int(n_qubits)
+        self.cfg = Config(int(chi_max), PRECISIONS[precision], float(trunc_rel), 1 if svd_fp64 else 0,
+                          int(svd_max_sweeps), float(svd_tol))
+        bits = None if init_bits is None else np.ascontiguousarray(init_bits, dtype=np.uint8)
+        h = ctypes.c_void_p()
+        _check(_lib.mps_create(ctx.handle, self.n, _ptr(bits), ctypes.byref(self.cfg), ctypes.byref(h)))
+        self.handle = h
+
+    def reset(self, init_bits=None):
+        bits = None if init_bits is None else np.ascontiguousarray(init_bits, dtype=np.uint8)
+        _check(_lib.mps_reset(self.handle, _ptr(bits)))
+
+    def apply_gates(self, gates) -> dict:
+        arr = gates_to_abi(gates)
+        rep = Report()
+        _check(_lib.mps_apply_gates(self.handle, _ptr(arr), arr.shape[0], ctypes.byref(rep)))
+        return rep.as_dict()
+
+    def apply_circuit(self, circuit: Circuit, theta, device_ptr: int = None):
+        """Bind theta (host array, or a device pointer to n_params doubles) and
+        apply the circuit; asynchronous on the context stream."""
+        if device_ptr is not None:
+            _check(_lib.mps_apply_circuit_async(self.handle, circuit.handle, ctypes.c_void_p(int(device_ptr)), 1))
+        else:
+            th = np.ascontiguousarray(theta, dtype=np.float64)
+            if th.shape != (circuit.n_params,):
+                raise ValueError(f"theta has shape {th.shape}, circuit takes ({circuit.n_params},)")
+            _check(_lib.mps_apply_circuit_async(self.handle, circuit.handle, _ptr(th), 0))
+
+    def energy(self, ham: Hamiltonian, with_norm: bool = False):
+        e, nrm = ctypes.c_double(), ctypes.c_double()
+        _check(_lib.mps_energy(self.handle, ham.handle, ctypes.byref(e), ctypes.byref(nrm) if with_norm else None))
+        return (e.value, nrm.value) if with_norm else e.value
+
+    def energy_async(self, ham: Hamiltonian, device_ptr: int):
+        _check(_lib.mps_energy_async(self.handle, ham.handle, ctypes.c_void_p(int(device_ptr))))
+
+    def expectations(self, ham: Hamiltonian) -> np.ndarray:
+        out = np.zeros(ham.n_terms)
+        _check(_lib.mps_expectations(self.handle, ham.handle, _ptr(out)))
+        return out
+
+    def bond_dims(self) -> np.ndarray:
+        out = np.zeros(self.n + 1, dtype=np.int32)
+        _check(_lib.mps_bond_dims(self.handle, _ptr(out)))
+        return out
+
+    def export(self):
+        """(list of B_n arrays (chi_l, 2, chi_r) complex128, list of lam_b arrays)."""
+        chi = self.bond_dims()
+        nt = int(sum(2 * chi[s] * 2 * chi[s + 1] for s in range(self.n)))
+        nl = int(chi.sum())
+        t = np.zeros(nt)
+        lam = np.zeros(nl)
+        _check(_lib.mps_export(self.handle, _ptr(t), nt, _ptr(lam), nl))
+        B, L = [], []
+        o = 0
+        for s in range(self.n):
+            cnt = chi[s] * 2 * chi[s + 1]
+            z = t[2 * o: 2 * (o + cnt)].view(np.complex128)
+            B.append(z.reshape(chi[s], 2, chi[s + 1]).copy())
+            o += cnt
+        o = 0
+        for b in range(self.n + 1):
+            L.append(lam[o: o + chi[b]].copy())
+            o += chi[b]
+        return B, L
+
+    def report(self) -> dict:
+        rep = Report()
+        _check(_lib.mps_get_report(self.handle, ctypes.byref(rep)))
+        return rep.as_dict()
+
+    def close(self):
+        if self.handle:
+            _lib.mps_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vqe_eval(ctx: Context, requests):
+    """requests: list of (State, Circuit, Hamiltonian, theta, init_bits or None).
+    Returns (energies, statuses)."""
+    n = len(requests)
+    reqs = (VqeRequest * n)()
+    keep = []
+    for i, (st, circ, ham, theta, bits) in enumerate(requests):
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        b = None if bits is None else np.ascontiguousarray(bits, dtype=np.uint8)
+        keep += [th, b]
+        reqs[i] = VqeRequest(st.handle.value, circ.handle.value, ham.handle.value, th.ctypes.data,
+                             None if b is None else b.ctypes.data)
+    energies = np.zeros(n)
+    status = np.zeros(n, dtype=np.int32)
+    rc = _lib.vqe_eval(ctx.handle, reqs, n, _ptr(energies), _ptr(status))
+    if rc != MPS_OK and np.all(status == MPS_OK):
+        _check(rc)
+    return energies, status
