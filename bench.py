@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Energy evaluations per second of the GB300 MPS-VQE hot path.
+
+One step = one VQE energy evaluation: reset the MPS to the Hartree-Fock
+state, apply the UCCSD-style circuit bound to a fresh theta, evaluate the
+Jordan-Wigner Pauli-sum energy (trie of shared left environments), FP64 sum.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2|c1]
+  python bench.py --impl reference ...   (the FP64 CPU oracle on a bounded sample)
+
+Under torchrun each rank evaluates its own instance (independent fragments,
+no collective on the data path: weak scaling); rank 0 prints one JSON line.
+"""
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2303_03681_gb300.inputs import (MASTER_SEED, brickwork_circuit, hf_bits, jw_molecular_hamiltonian,  # noqa: E402
+                                           make_rng, random_integrals, uccsd_template)
+from paper_2303_03681_gb300.inputs.circuits import CircuitTemplate, uccsd_excitations  # noqa: E402
+
+METRIC = "energy evals/s"
+# derived ALU peaks (152 SMs x 2070 MHz): FP32 128 FMA/clk/SM, FP64 2 FMA/clk/SM
+SM_COUNT, SM_MHZ = 152, 2070.0
+ALU_PEAK_TFLOPS = {"f32": SM_COUNT * 128 * 2 * SM_MHZ * 1e6 / 1e12, "f64": SM_COUNT * 2 * 2 * SM_MHZ * 1e6 / 1e12}
+
+
+def build_workload(name, args, rank):
+    """Seeded synthetic inputs of a named configuration."""
+    if name == "c2":
+        n_orb, n_e, chi = 25, 10, 128
+        n_exc = args.excitations
+        h, g = random_integrals(n_orb, make_rng(MASTER_SEED + 11))
+        ham = jw_molecular_hamiltonian(h, g)
+        tmpl = uccsd_template(2 * n_orb, n_e, max_excitations=n_exc)
+        total_exc = len(uccsd_excitations(2 * n_orb, n_e))
+        bits = hf_bits(2 * n_orb, n_e)
+        desc = dict(workload=f"c2_uccsd_{2 * n_orb}q_chi{chi}_first{n_exc}exc",
+                    n_qubits=2 * n_orb, chi_max=chi, n_terms=int(ham.n_terms),
+                    excitations=f"first {n_exc} of {total_exc} (singles first)",
+                    two_qubit_gates=int(tmpl.n_two_qubit), trunc_rel=args.trunc_rel,
+                    hamiltonian="JW of random 25-orbital integrals, h~N(0,1), (pq|rs)~N(0,0.1^2) 8-fold",
+                    theta="U[-0.05, 0.05] per excitation, new draw per step")
+        return dict(ham=ham, tmpl=tmpl, bits=bits, chi=chi, trunc=args.trunc_rel, theta_scale=0.05,
+                    precision=args.precision or "fp32", desc=desc)
+    if name == "c1":
+        h, g = random_integrals(6, make_rng(MASTER_SEED))
+        ham = jw_molecular_hamiltonian(h, g)
+        gl = brickwork_circuit(12, 8, make_rng(MASTER_SEED + 1))
+        tmpl = CircuitTemplate.from_gates(gl)
+        desc = dict(workload="c1_brickwork_12q_8layers_chi64", n_qubits=12, chi_max=64, n_terms=int(ham.n_terms),
+                    two_qubit_gates=44, trunc_rel=0.0)
+        return dict(ham=ham, tmpl=tmpl, bits=hf_bits(12, 6), chi=64, trunc=0.0, theta_scale=0.0,
+                    precision=args.precision or "fp64", desc=desc)
+    raise SystemExit(f"unknown workload {name}")
+
+
+def thetas_for(w, count, seed):
+    rng = make_rng(seed)
+    n = max(1, w["tmpl"].n_params)
+    return [rng.uniform(-w["theta_scale"], w["theta_scale"], n)[: w["tmpl"].n_params] for _ in range(count)]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    d = os.path.join(ROOT, "paper_2303_03681_gb300", "csrc")
+    hsh = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            hsh.update(open(os.path.join(d, f), "rb").read())
+    return hsh.hexdigest()[:16]
+
+
+def recorded_traffic(kind, workload):
+    """DRAM bytes per launch from a committed ncu summary of the same kernel source, else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        rec = json.load(open(p))
+    except ValueError:
+        return None
+    e = rec.get(f"{kind}:{workload}")
+    if e and e.get("source_sha") == kernel_source_hash():
+        return e.get("dram_bytes_per_launch")
+    return None
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (bounded sample)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(w, budget_gates_s=8.0, budget_terms_s=6.0, seed=0):
+    """Times the FP64 oracle on the first gates of the step's circuit and on a
+    sample of its Pauli terms; extrapolates one step linearly.  The sample's
+    bond dimensions are those reached after its first gates, so the estimate is
+    a lower bound on the oracle's time per step."""
+    from oracle import mps as om
+
+    theta = thetas_for(w, 1, seed)[0]
+    gates = w["tmpl"].bind(theta)
+    st = om.product_state(w["bits"])
+    t0 = time.perf_counter()
+    done = 0
+    while done < gates.n_gates and time.perf_counter() - t0 < budget_gates_s:
+        q = int(gates.q[done])
+        if gates.arity[done] == 1:
+            om.apply_1q(st, q, gates.u[done][:2, :2])
+        else:
+            om.apply_2q(st, q, gates.u[done], w["chi"], w["trunc"])
+        done += 1
+    t_g = time.perf_counter() - t0
+    rng = make_rng(seed + 1)
+    order = rng.permutation(w["ham"].n_terms)
+    t0 = time.perf_counter()
+    nt = 0
+    while nt < order.size and time.perf_counter() - t0 < budget_terms_s:
+        om.expect_pauli(st, w["ham"].ops[order[nt]])
+        nt += 1
+    t_t = time.perf_counter() - t0
+    step_s = t_g / max(done, 1) * gates.n_gates + t_t / max(nt, 1) * w["ham"].n_terms
+    sample = (f"oracle on the first {done} of {gates.n_gates} gates ({t_g:.1f} s, chi reached "
+              f"{max(st.bond_dims())}) and {nt} of {w['ham'].n_terms} terms ({t_t:.1f} s), extrapolated linearly "
+              f"to one step")
+    return step_s, sample
+
+
+def blas_threads():
+    try:
+        from threadpoolctl import threadpool_info
+
+        return max((i.get("num_threads", 1) for i in threadpool_info()), default=1)
+    except Exception:
+        return int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = build_workload(args.workload, args, 0)
+    for _ in range(args.warmup):
+        oracle_sample(w, 2.0, 1.0)
+    times, sample = [], ""
+    for k in range(args.steps):
+        s, sample = oracle_sample(w, 8.0, 6.0, seed=k)
+        times.append(s)
+    step_s = float(np.mean(times))
+    v = 1.0 / step_s
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": w["desc"],
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": blas_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2303_03681_gb300 import mps
+
+    w = build_workload(args.workload, args, rank)
+    stream = torch.cuda.current_stream()
+    ctx = mps.Context(local, stream=stream)
+    H = mps.Hamiltonian(ctx, w["ham"])
+    C = mps.Circuit(ctx, w["tmpl"])
+    svd64 = args.svd == "fp64"
+    st = mps.State(ctx, w["tmpl"].n_qubits, w["bits"], chi_max=w["chi"], precision=w["precision"],
+                   trunc_rel=w["trunc"], svd_fp64=svd64)
+    n_steps = args.warmup + args.steps
+    thetas = thetas_for(w, n_steps + args.steps, MASTER_SEED + 1000 * (rank + 1))
+    d_theta = torch.tensor(np.stack(thetas[:n_steps]) if w["tmpl"].n_params else np.zeros((n_steps, 1)),
+                           dtype=torch.float64, device=f"cuda:{local}")
+    d_energy = torch.zeros(n_steps, dtype=torch.float64, device=f"cuda:{local}")
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=f"cuda:{local}")  # 256 MB > 129 MB L2
+
+    def step(i):
+        st.reset(w["bits"])
+        st.apply_circuit(C, None, device_ptr=d_theta[i].data_ptr())
+        st.energy_async(H, d_energy[i:i + 1].data_ptr())
+
+    ctx.profile(mps.KERNEL_KINDS)
+    for i in range(args.warmup):
+        flush.zero_()
+        step(i)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read(reset=True)
+    dominant = max(prof, key=lambda k: prof[k][2])
+    ctx.profile([dominant])
+    st.reset(w["bits"])
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(local) as clocks:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()  # L2 flush between timed steps, outside the events
+            events[k][0].record(stream)
+            step(args.warmup + k)
+            events[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    rep = st.report()  # statistics of the last step only
+    svd_flops_last = rep["svd_flops"]
+    step_ms = [a.elapsed_time(b) for a, b in events]
+    total_s = sum(step_ms) / 1e3
+    if dist:
+        t = torch.tensor([total_s], device=f"cuda:{local}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    kprof = ctx.profile_read(reset=True)
+    energies = d_energy.cpu().numpy()
+
+    # end to end through the C-ABI with host buffers: theta H2D, energy D2H
+    e2e_times = []
+    host_thetas = thetas[n_steps:n_steps + args.steps]
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e, status = mps.vqe_eval(ctx, [(st, C, H, host_thetas[k], w["bits"])])
+        e2e_times.append(time.perf_counter() - t0)
+        assert status[0] == 0
+    e2e_s = sum(e2e_times)
+    if dist:
+        t = torch.tensor([e2e_s], device=f"cuda:{local}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    value = world * args.steps / total_s
+    launches_per_step = sum(v[0] for v in kprof.values()) / args.steps
+    dom_launches, dom_timed, dom_ms = kprof[dominant]
+    roofline = None
+    if dom_timed:
+        avg_s = dom_ms / 1e3 / dom_timed
+        per_step = dom_timed / args.steps
+        if dominant == "svd":
+            dt = "f64" if svd64 else "f32"
+            flops = svd_flops_last / max(per_step, 1)
+            achieved = flops / avg_s / 1e12
+            peak = ALU_PEAK_TFLOPS[dt]
+            roofline = {"bound": "alu", "kernel": "svd_truncate_kernel", "achieved": achieved, "peak": peak,
+                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": recorded_traffic(dominant,
+                                                                                                 w["desc"]["workload"]),
+                        "avg_launch_us": avg_s * 1e6, "launches_per_step": per_step,
+                        "peak_source": f"derived {dt.upper()} ALU peak: {SM_COUNT} SMs x "
+                                       f"{'128' if dt == 'f32' else '2'} FMA/clk x {SM_MHZ:.0f} MHz",
+                        "work": "Jacobi flops actually run (sweeps x pairs x (16m + 12(m+n))) / launch"}
+        else:
+            roofline = {"bound": "alu", "kernel": dominant, "achieved": None, "peak": None, "unit": "TFLOP/s",
+                        "frac": None, "traffic": None, "avg_launch_us": avg_s * 1e6, "launches_per_step": per_step}
+    line = {
+        "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64" if w["precision"] == "fp32" else "c128",
+        "data": "synthetic",
+        "config": dict(w["desc"], precision=f"{w['precision']} storage/contractions, {args.svd} Jacobi SVD, "
+                                            f"FP64 energy sum", l2="flushed between steps (256 MB write)",
+                       parallelism=f"replicas x{world}"),
+        "e2e": {"value": world * args.steps / e2e_s, "unit": "evals/s",
+                "h2d_bytes_per_step": 8 * w["tmpl"].n_params, "d2h_bytes_per_step": 8},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "roofline": roofline,
+        "clocks": clocks.summary(),
+        "kernel_time_share": {k: round(v[2] / max(1e-9, sum(x[2] for x in prof.values())), 4)
+                              for k, v in prof.items() if v[2] > 0},
+        "energies": [float(x) for x in energies[args.warmup:args.warmup + 3]],
+        "last_step_report": {k: rep[k] for k in ("max_chi", "discarded_weight", "svd_not_converged",
+                                                   "degenerate_cuts", "two_qubit_gates")},
+        "wall_s_timed_region": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        step_s, sample = oracle_sample(w)
+        line["cpu_baseline"] = {"value": 1.0 / step_s, "unit": "evals/s", "cores": blas_threads(), "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--excitations", type=int, default=200)
+    ap.add_argument("--trunc-rel", type=float, default=1e-5)
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default=None)
+    ap.add_argument("--svd", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -96,7 +96,23 @@ typedef struct {
   int32_t svd_not_converged;/* SVDs that hit the sweep cap */
   int32_t max_sweeps_used;  /* largest number of Jacobi sweeps of one SVD */
   int64_t two_qubit_gates;  /* two-qubit gates applied */
+  double svd_flops;         /* real flops of the Jacobi sweeps run (dots + rotations) */
 } mps_report;
+
+/* Kernel classes for mps_ctx_profile_read. */
+typedef enum {
+  MPS_K_THETA = 0,     /* theta contraction + gate + lam scaling */
+  MPS_K_SVD = 1,       /* Jacobi SVD + truncation */
+  MPS_K_G3 = 2,        /* B~_q = C V^dagger */
+  MPS_K_GATE1 = 3,     /* one-qubit gate */
+  MPS_K_SETUP = 4,     /* reset, angle binding, fills */
+  MPS_K_ENV_M = 5,     /* environment times site tensor */
+  MPS_K_ENV_CHILD = 6, /* child environment */
+  MPS_K_ENV_LEAF = 7,  /* leaf expectation values */
+  MPS_K_ENV_TRACE = 8, /* trace expectation values */
+  MPS_K_REDUCE = 9,    /* FP64 energy sum */
+  MPS_K_COUNT = 10
+} mps_kernel_kind;
 
 typedef struct mps_ctx mps_ctx;
 typedef struct mps_state mps_state;
@@ -117,7 +133,17 @@ mps_status mps_ctx_synchronize(mps_ctx* ctx);
  * allocation beyond it fails with MPS_ENOMEM. */
 mps_status mps_ctx_set_alloc_limit(mps_ctx* ctx, size_t bytes);
 mps_status mps_ctx_bytes_allocated(const mps_ctx* ctx, size_t* out);
+/* Destroys the context and frees its device memory.  Destroy its states,
+ * Hamiltonians and circuits first: their handles become invalid. */
 void mps_ctx_destroy(mps_ctx* ctx);
+/* Kernel timing: for every kernel class whose bit is set in `mask`
+ * (bit k = mps_kernel_kind k) the library brackets each launch with CUDA
+ * events on the context stream.  Launch counts are always kept. */
+mps_status mps_ctx_profile(mps_ctx* ctx, uint32_t mask);
+/* Launches of class `kind` and their summed device time (ms, timed launches
+ * only) since the last reset; synchronises the stream.  reset != 0 clears. */
+mps_status mps_ctx_profile_read(mps_ctx* ctx, int32_t kind, int64_t* launches, int64_t* timed_launches,
+                                double* ms, int32_t reset);
 
 /* Create an n-qubit MPS in the computational basis state |init_bits>
  * (init_bits: n bytes, 0/1; NULL = |0...0>) - the chi = 1 product state of

@@ -27,6 +27,9 @@ def one_sided_jacobi_svd(A: np.ndarray, eps: float = 1e-15, max_sweeps: int = 60
         return Vh.conj().T, s, U.conj().T
     V = np.eye(n, dtype=complex)
     tiny = np.finfo(float).tiny
+    # columns at the rounding level of A are left alone (a rotation between
+    # two of them only reshuffles rounding noise)
+    floor = (eps * np.linalg.norm(A)) ** 2
     for _ in range(max_sweeps):
         rotated = False
         for i in range(n - 1):
@@ -36,7 +39,7 @@ def one_sided_jacobi_svd(A: np.ndarray, eps: float = 1e-15, max_sweeps: int = 60
                 bjj = float(np.vdot(aj, aj).real)
                 bij = complex(np.vdot(ai, aj))
                 mag = abs(bij)
-                if mag <= tiny or mag < eps * np.sqrt(bii * bjj):
+                if mag <= tiny or mag < eps * np.sqrt(bii * bjj) or min(bii, bjj) <= floor:
                     continue
                 rotated = True
                 ph = bij / mag

@@ -110,6 +110,7 @@ struct DevReport {
   int not_converged;
   int max_sweeps;
   long long two_qubit_gates;
+  double svd_flops;
 };
 
 // Parameters of the truncation SVD.

@@ -124,12 +124,14 @@ static mps_status build_trie(mps_ham* h, const uint8_t* ops, const double* coeff
   return MPS_OK;
 }
 
+// Environment buffers sized for the bond dimensions the state has now
+// (grow-only); slot strides follow the same dimensions.
 template <typename R>
-static mps_status ensure_env_buffers(mps_state* st, mps_ham* h) {
+static mps_status ensure_env_buffers(const std::vector<int>& chi, mps_ham* h) {
   size_t Lneed = 16, Mneed = 16;
   for (int j = 0; j < h->n; ++j) {
     const LevelHost& L = h->levels[j];
-    const size_t cl = st->cap[j], cr = st->cap[j + 1];
+    const size_t cl = chi[j], cr = chi[j + 1];
     Lneed = std::max(Lneed, (size_t)L.n_children * cr * cr * sizeof(cplx<R>));
     Mneed = std::max(Mneed, (size_t)L.n_parents * 2 * cl * cr * sizeof(cplx<R>));
   }
@@ -157,11 +159,26 @@ static mps_status ensure_env_buffers(mps_state* st, mps_ham* h) {
 
 template <typename R>
 static mps_status energy_levels(mps_state* st, mps_ham* h, double* d_out) {
-  mps_status rc = ensure_env_buffers<R>(st, h);
-  if (rc != MPS_OK) return rc;
   cudaStream_t s = st->ctx->stream;
+  // One read of the bond dimensions sizes every grid of this evaluation.
+  std::vector<int> chi(st->n + 1);
+  MPSV_CUDA(cudaMemcpyAsync(chi.data(), st->d_chi, (st->n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s));
+  MPSV_CUDA(cudaStreamSynchronize(s));
+  for (int b = 0; b <= st->n; ++b) {
+    if (chi[b] < 1 || chi[b] > st->cap[b]) {
+      set_error("energy: bond %d has dimension %d outside 1..%d (state corrupted)", b, chi[b], st->cap[b]);
+      st->broken = true;
+      return MPS_ESTATE;
+    }
+  }
+  mps_status rc = ensure_env_buffers<R>(chi, h);
+  if (rc != MPS_OK) return rc;
   const long long nt = h->n_terms;
-  if (nt) fill_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(h->d_vals, nt, 1.0);
+  mps_ctx* c = st->ctx;
+  if (nt) {
+    KernelScope k(c, MPS_K_SETUP);
+    fill_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(h->d_vals, nt, 1.0);
+  }
   const cplx<R>* B = reinterpret_cast<const cplx<R>*>(st->d_B);
   cplx<R>* Lprev = reinterpret_cast<cplx<R>*>(h->d_L[0]);
   cplx<R>* Lcur = reinterpret_cast<cplx<R>*>(h->d_L[1]);
@@ -180,19 +197,33 @@ static mps_status energy_levels(mps_state* st, mps_ham* h, double* d_out) {
     lv.n_leaves = L.n_leaves;
     lv.n_traces = L.n_traces;
     lv.site = j;
-    lv.cap_l = st->cap[j];
-    lv.cap_r = st->cap[j + 1];
+    lv.cap_l = chi[j];
+    lv.cap_r = chi[j + 1];
     const cplx<R>* Bj = B + st->site_off[j];
     const int tl = (lv.cap_l + kTile - 1) / kTile, tr = (lv.cap_r + kTile - 1) / kTile;
-    env_m_kernel<R><<<(unsigned)((size_t)L.n_parents * tl * tr), blk, 0, s>>>(
-        Lprev, Bj, st->d_lam + st->lam_off[j], st->d_chi, lv, M);
-    if (L.n_children)
+    {
+      KernelScope k(c, MPS_K_ENV_M);
+      env_m_kernel<R><<<(unsigned)((size_t)L.n_parents * tl * tr), blk, 0, s>>>(
+          Lprev, Bj, st->d_lam + st->lam_off[j], st->d_chi, lv, M);
+    }
+    if (L.n_children) {
+      KernelScope k(c, MPS_K_ENV_CHILD);
       env_child_kernel<R><<<(unsigned)((size_t)L.n_children * tr * tr), blk, 0, s>>>(M, Bj, st->d_chi, lv, Lcur);
-    if (L.n_leaves) env_leaf_kernel<R><<<(L.n_leaves + 7) / 8, 256, 0, s>>>(M, Bj, st->d_chi, lv, h->d_vals);
-    if (L.n_traces) env_trace_kernel<R><<<(L.n_traces + 7) / 8, 256, 0, s>>>(Lcur, st->d_chi, lv, h->d_vals);
+    }
+    if (L.n_leaves) {
+      KernelScope k(c, MPS_K_ENV_LEAF);
+      env_leaf_kernel<R><<<(L.n_leaves + 7) / 8, 256, 0, s>>>(M, Bj, st->d_chi, lv, h->d_vals);
+    }
+    if (L.n_traces) {
+      KernelScope k(c, MPS_K_ENV_TRACE);
+      env_trace_kernel<R><<<(L.n_traces + 7) / 8, 256, 0, s>>>(Lcur, st->d_chi, lv, h->d_vals);
+    }
     if (L.n_children) std::swap(Lprev, Lcur);
   }
-  energy_reduce_kernel<<<1, 1024, 0, s>>>(h->d_vals, h->d_coeffs, nt, 0.0, d_out);
+  {
+    KernelScope k(c, MPS_K_REDUCE);
+    energy_reduce_kernel<<<1, 1024, 0, s>>>(h->d_vals, h->d_coeffs, nt, 0.0, d_out);
+  }
   MPSV_CUDA(cudaGetLastError());
   return MPS_OK;
 }

@@ -48,7 +48,7 @@ struct EnvLevel {
   const int2* trace;      // per string ending at a materialised node: (slot, term)
   int n_parents, n_children, n_leaves, n_traces;
   int site;
-  int cap_l, cap_r;  // bond capacities left / right of the site
+  int cap_l, cap_r;  // bond dimensions left / right of the site at launch (grid extents and slot strides)
 };
 
 // M^b_p[a][d] = sum_c L_p[a][c] B[c][b][d]   (b = 0, 1);  slot stride of M: 2 cap_l cap_r

@@ -48,6 +48,7 @@ __global__ void reset_kernel(cplx<R>* __restrict__ B, const size_t* __restrict__
     rep->not_converged = 0;
     rep->max_sweeps = 0;
     rep->two_qubit_gates = 0;
+    rep->svd_flops = 0.0;
   }
 }
 
@@ -149,8 +150,11 @@ template <> struct SvdEps<float> {
 
 // Jacobi sweeps on A (m x n, column-major) accumulating V (n x n, column-major).
 // Returns the number of sweeps used (max_sweeps + 1 if not converged).
+// Columns whose squared norm is at most `floor` (the rounding level of A)
+// are left alone: rotating two of them only reshuffles rounding noise, and a
+// rotation against a larger column would move it by less than that noise.
 template <typename S>
-__device__ int jacobi_sweeps(cplx<S>* A, cplx<S>* V, int m, int n, int max_sweeps, S tol, int* s_flag) {
+__device__ int jacobi_sweeps(cplx<S>* A, cplx<S>* V, int m, int n, int max_sweeps, S tol, S floor, int* s_flag) {
   using C = cplx<S>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int nn = n + (n & 1);
@@ -181,7 +185,7 @@ __device__ int jacobi_sweeps(cplx<S>* A, cplx<S>* V, int m, int n, int max_sweep
         gam.x = warp_sum(gam.x);
         gam.y = warp_sum(gam.y);
         const S mag = sqrt(gam.x * gam.x + gam.y * gam.y);
-        if (!(mag > tiny) || !(mag > tol * sqrt(alpha * beta))) continue;
+        if (!(mag > tiny) || !(mag > tol * sqrt(alpha * beta)) || !(min(alpha, beta) > floor)) continue;
         rotated = true;
         const C ph = cmk<S>(gam.x / mag, gam.y / mag);
         const S zeta = (beta - alpha) / (S(2) * mag);
@@ -252,7 +256,23 @@ __global__ void __launch_bounds__(1024, 1)
   __syncthreads();
 
   const S tol = p.tol > 0 ? S(p.tol) : S(max(m, n)) * SvdEps<S>::unit();
-  const int sweeps = jacobi_sweeps<S>(A, V, m, n, p.max_sweeps, tol, &s_flag);
+  // ||A||_F^2 sets the noise floor of a column
+  {
+    double part = 0.0;
+    for (size_t t = threadIdx.x; t < (size_t)m * n; t += blockDim.x) {
+      const double x = A[t].x, y = A[t].y;
+      part += x * x + y * y;
+    }
+    part = warp_sum(part);
+    if (threadIdx.x == 0) s_nrm = 0.0;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s_nrm, part);
+    __syncthreads();
+  }
+  const double fro2 = s_nrm;
+  const S floor = S(double(tol) * double(tol) * fro2);
+  __syncthreads();
+  const int sweeps = jacobi_sweeps<S>(A, V, m, n, p.max_sweeps, tol, floor, &s_flag);
 
   // sigma_j = ||A_j|| (Algorithm 1: column norms)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -306,6 +326,9 @@ __global__ void __launch_bounds__(1024, 1)
     if (sweeps > p.max_sweeps) rep->not_converged += 1;
     if (sweeps > rep->max_sweeps) rep->max_sweeps = sweeps;
     rep->two_qubit_gates += 1;
+    // per sweep and column pair: three dot products over m rows (16 m flops)
+    // and one rotation of the A and V columns (12 (m + n) flops)
+    rep->svd_flops += (double)min(sweeps, p.max_sweeps) * 0.5 * n * (n - 1) * (16.0 * m + 12.0 * (m + n));
     rep->inv_norm = 1.0 / nrm;
     chi[q + 1] = k;
   }

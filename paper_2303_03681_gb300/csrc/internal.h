@@ -45,7 +45,29 @@ struct mps_ctx {
   size_t alloc_limit = 0;
   size_t allocated = 0;
   std::map<void*, size_t> allocs;
+  // kernel accounting (mps_ctx_profile)
+  uint32_t prof_mask = 0;
+  long long launches[MPS_K_COUNT] = {};
+  long long timed[MPS_K_COUNT] = {};
+  double ms[MPS_K_COUNT] = {};
+  struct Pending {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
 };
+
+namespace mpsv {
+// Bracket one kernel launch for accounting: KernelScope k(ctx, kind); launch<<<...>>>;
+struct KernelScope {
+  mps_ctx* c;
+  int kind;
+  cudaEvent_t a = nullptr, b = nullptr;
+  KernelScope(mps_ctx* ctx, int k);
+  ~KernelScope();
+};
+}  // namespace mpsv
 
 namespace mpsv {
 mps_status dev_alloc(mps_ctx* ctx, void** p, size_t bytes);

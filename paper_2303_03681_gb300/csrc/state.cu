@@ -56,6 +56,46 @@ void dev_free(mps_ctx* ctx, void* p) {
   cudaFree(p);
 }
 
+KernelScope::KernelScope(mps_ctx* ctx, int k) : c(ctx), kind(k) {
+  c->launches[k] += 1;
+  if (!(c->prof_mask & (1u << k))) return;
+  for (cudaEvent_t* e : {&a, &b}) {
+    if (!c->pool.empty()) {
+      *e = c->pool.back();
+      c->pool.pop_back();
+    } else if (cudaEventCreate(e) != cudaSuccess) {
+      cudaGetLastError();
+      *e = nullptr;
+    }
+  }
+  if (a && b) cudaEventRecord(a, c->stream);
+}
+
+KernelScope::~KernelScope() {
+  if (!a || !b) {
+    if (a) c->pool.push_back(a);
+    if (b) c->pool.push_back(b);
+    return;
+  }
+  cudaEventRecord(b, c->stream);
+  c->pending.push_back({kind, a, b});
+}
+
+static void collect_profile(mps_ctx* c) {
+  for (auto& p : c->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      c->ms[p.kind] += ms;
+      c->timed[p.kind] += 1;
+    } else {
+      cudaGetLastError();
+    }
+    c->pool.push_back(p.a);
+    c->pool.push_back(p.b);
+  }
+  c->pending.clear();
+}
+
 static int bond_cap(int b, int n, int chi_max) {
   int e = std::min(b, n - b);
   if (e >= 30) return chi_max;
@@ -100,9 +140,12 @@ static void launch_two_qubit(mps_state* st, const DevGate* g, int q, cudaStream_
   const int cap_l = st->cap[q], cap_m = st->cap[q + 1], cap_r = st->cap[q + 2];
   const dim3 blk(kTile, kTile);
   const dim3 g1((cap_r + kTile - 1) / kTile, (cap_l + kTile - 1) / kTile);
-  theta_kernel<R, S><<<g1, blk, 0, s>>>(site_ptr<R>(st, q), site_ptr<R>(st, q + 1), g, st->d_lam + st->lam_off[q],
-                                        st->d_chi, q, reinterpret_cast<cplx<R>*>(st->d_C),
-                                        reinterpret_cast<cplx<S>*>(st->d_A));
+  {
+    KernelScope k(st->ctx, MPS_K_THETA);
+    theta_kernel<R, S><<<g1, blk, 0, s>>>(site_ptr<R>(st, q), site_ptr<R>(st, q + 1), g,
+                                          st->d_lam + st->lam_off[q], st->d_chi, q,
+                                          reinterpret_cast<cplx<R>*>(st->d_C), reinterpret_cast<cplx<S>*>(st->d_A));
+  }
   const int mcap = 2 * cap_l, ncap = 2 * cap_r;
   const size_t full = svd_smem_bytes<S>(mcap, ncap, true);
   const bool use_smem = full + 2048 <= max_dyn_smem();
@@ -114,17 +157,24 @@ static void launch_two_qubit(mps_state* st, const DevGate* g, int q, cudaStream_
   p.max_sweeps = st->cfg.svd_max_sweeps > 0 ? st->cfg.svd_max_sweeps : 60;
   p.trunc_rel = st->cfg.trunc_rel;
   p.tol = st->cfg.svd_tol;
-  svd_truncate_kernel<S, R><<<1, 32 * warps, smem, s>>>(
-      reinterpret_cast<cplx<S>*>(st->d_A), reinterpret_cast<cplx<S>*>(st->d_V), use_smem ? 1 : 0, st->d_chi, q, p,
-      site_ptr<R>(st, q + 1), st->d_lam + st->lam_off[q + 1], st->d_rep);
+  {
+    KernelScope k(st->ctx, MPS_K_SVD);
+    svd_truncate_kernel<S, R><<<1, 32 * warps, smem, s>>>(
+        reinterpret_cast<cplx<S>*>(st->d_A), reinterpret_cast<cplx<S>*>(st->d_V), use_smem ? 1 : 0, st->d_chi, q,
+        p, site_ptr<R>(st, q + 1), st->d_lam + st->lam_off[q + 1], st->d_rep);
+  }
   const dim3 g3((cap_m + kTile - 1) / kTile, (2 * cap_l + kTile - 1) / kTile);
-  g3_kernel<R><<<g3, blk, 0, s>>>(reinterpret_cast<cplx<R>*>(st->d_C), site_ptr<R>(st, q + 1), st->d_chi, q,
-                                  st->d_rep, site_ptr<R>(st, q));
+  {
+    KernelScope k(st->ctx, MPS_K_G3);
+    g3_kernel<R><<<g3, blk, 0, s>>>(reinterpret_cast<cplx<R>*>(st->d_C), site_ptr<R>(st, q + 1), st->d_chi, q,
+                                    st->d_rep, site_ptr<R>(st, q));
+  }
 }
 
 template <typename R>
 static void launch_one_qubit(mps_state* st, const DevGate* g, int q, cudaStream_t s) {
   const int tot = st->cap[q] * st->cap[q + 1];
+  KernelScope k(st->ctx, MPS_K_GATE1);
   gate1_kernel<R><<<(tot + 255) / 256, 256, 0, s>>>(site_ptr<R>(st, q), g, st->d_chi, q);
 }
 
@@ -174,6 +224,7 @@ mps_status state_reset(mps_state* st, const uint8_t* bits) {
     st->last_bits = hb;
   }
   const int threads = 256, blocks = (st->n + 1 + threads - 1) / threads;
+  KernelScope k(st->ctx, MPS_K_SETUP);
   if (st->fp32)
     reset_kernel<float><<<blocks, threads, 0, s>>>(reinterpret_cast<float2*>(st->d_B), st->d_site_off, st->d_lam,
                                                    st->d_lam_off, st->d_chi, st->d_bits, st->n, st->d_rep);
@@ -273,10 +324,41 @@ mps_status mps_ctx_bytes_allocated(const mps_ctx* ctx, size_t* out) {
   return MPS_OK;
 }
 
+mps_status mps_ctx_profile(mps_ctx* ctx, uint32_t mask) {
+  if (!ctx) {
+    set_error("mps_ctx_profile: NULL context");
+    return MPS_EINVAL;
+  }
+  ctx->prof_mask = mask;
+  return MPS_OK;
+}
+
+mps_status mps_ctx_profile_read(mps_ctx* ctx, int32_t kind, int64_t* launches, int64_t* timed_launches, double* ms,
+                                int32_t reset) {
+  if (!ctx || kind < 0 || kind >= MPS_K_COUNT) {
+    set_error("mps_ctx_profile_read: NULL context or kind %d outside 0..%d", kind, MPS_K_COUNT - 1);
+    return MPS_EINVAL;
+  }
+  DeviceGuard guard(ctx->device);
+  MPSV_CUDA(cudaStreamSynchronize(ctx->stream));
+  collect_profile(ctx);
+  if (launches) *launches = ctx->launches[kind];
+  if (timed_launches) *timed_launches = ctx->timed[kind];
+  if (ms) *ms = ctx->ms[kind];
+  if (reset) {
+    ctx->launches[kind] = 0;
+    ctx->timed[kind] = 0;
+    ctx->ms[kind] = 0.0;
+  }
+  return MPS_OK;
+}
+
 void mps_ctx_destroy(mps_ctx* ctx) {
   if (!ctx) return;
   DeviceGuard guard(ctx->device);
   cudaStreamSynchronize(ctx->stream);
+  collect_profile(ctx);
+  for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
   for (auto& kv : ctx->allocs) cudaFree(kv.first);
   ctx->allocs.clear();
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
@@ -402,6 +484,7 @@ mps_status mps_get_report(mps_state* st, mps_report* out) {
   out->svd_not_converged = r.not_converged;
   out->max_sweeps_used = r.max_sweeps;
   out->two_qubit_gates = r.two_qubit_gates;
+  out->svd_flops = r.svd_flops;
   return MPS_OK;
 }
 
@@ -609,7 +692,10 @@ mps_status mps_apply_circuit_async(mps_state* st, const mps_circuit* c, const do
     d_theta = c->d_theta;
   }
   if (c->n_gates) {
-    bind_kernel<<<c->n_gates, 32, 0, s>>>(c->d_tmpl, c->n_gates, d_theta ? d_theta : c->d_theta, c->d_bound);
+    {
+      KernelScope k(st->ctx, MPS_K_SETUP);
+      bind_kernel<<<c->n_gates, 32, 0, s>>>(c->d_tmpl, c->n_gates, d_theta ? d_theta : c->d_theta, c->d_bound);
+    }
     mps_status rc = state_apply_device_gates(st, c->d_bound, c->q.data(), c->arity.data(), c->n_gates);
     if (rc != MPS_OK) {
       st->broken = true;

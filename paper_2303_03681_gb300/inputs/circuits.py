@@ -88,7 +88,10 @@ class CircuitTemplate:
         theta = np.asarray(theta, dtype=float)
         if theta.shape != (self.n_params,):
             raise ValueError(f"theta has shape {theta.shape}, expected ({self.n_params},)")
-        phi = np.where(self.param >= 0, self.coeff * theta[np.maximum(self.param, 0)], 0.0)
+        if self.n_params == 0:
+            phi = np.zeros(self.n_gates)
+        else:
+            phi = np.where(self.param >= 0, self.coeff * theta[np.maximum(self.param, 0)], 0.0)
         u = (np.exp(1j * phi)[:, None, None] * self.m_plus
              + np.exp(-1j * phi)[:, None, None] * self.m_minus)
         return GateList(self.n_qubits, self.q.copy(), self.arity.copy(), u)

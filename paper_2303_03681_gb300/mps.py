@@ -5,8 +5,10 @@ fallback.  Importing this module loads the library and raises if it is
 missing or cannot be loaded.
 """
 
+import atexit
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -17,6 +19,7 @@ MPS_OK, MPS_EINVAL, MPS_ENOMEM, MPS_ECUDA, MPS_ETIMEOUT, MPS_ENOTCONV, MPS_EBUSY
 STATUS_NAMES = ["MPS_OK", "MPS_EINVAL", "MPS_ENOMEM", "MPS_ECUDA", "MPS_ETIMEOUT", "MPS_ENOTCONV", "MPS_EBUSY",
                 "MPS_ESTATE"]
 PRECISIONS = {"fp64": 0, "fp32": 1}
+KERNEL_KINDS = ["theta", "svd", "g3", "gate1", "setup", "env_m", "env_child", "env_leaf", "env_trace", "reduce"]
 
 # numpy views of the C structs (layouts match include/mps_vqe.h on LP64 hosts)
 GATE_DTYPE = np.dtype([("q", "<i4"), ("arity", "<i4"), ("u", "<f8", (32,))])
@@ -40,7 +43,7 @@ class Report(ctypes.Structure):
     _fields_ = [("discarded_weight", ctypes.c_double), ("min_kept_sv", ctypes.c_double),
                 ("max_chi", ctypes.c_int32), ("degenerate_cuts", ctypes.c_int32),
                 ("svd_not_converged", ctypes.c_int32), ("max_sweeps_used", ctypes.c_int32),
-                ("two_qubit_gates", ctypes.c_int64)]
+                ("two_qubit_gates", ctypes.c_int64), ("svd_flops", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -84,6 +87,9 @@ def _load():
         "mps_export": ([P, P, SZ, P, SZ], ctypes.c_int),
         "mps_get_report": ([P, ctypes.POINTER(Report)], ctypes.c_int),
         "vqe_eval": ([P, P, SZ, P, P], ctypes.c_int),
+        "mps_ctx_profile": ([P, ctypes.c_uint32], ctypes.c_int),
+        "mps_ctx_profile_read": ([P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                  ctypes.POINTER(D), I32], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -152,6 +158,45 @@ def template_to_abi(tmpl) -> np.ndarray:
 # ---------------------------------------------------------------------------
 # handles
 # ---------------------------------------------------------------------------
+#
+# A context owns the device memory of its states, Hamiltonians and circuits.
+# Children are released before their context whatever order Python finalises
+# them in (at interpreter exit reference cycles are collected in arbitrary
+# order): Context.close() closes its live children first, and a child whose
+# context is already closed only drops its handle.
+
+_live_contexts = weakref.WeakSet()
+
+
+@atexit.register
+def _close_all_contexts():
+    for c in list(_live_contexts):
+        try:
+            c.close()
+        except Exception:
+            pass
+
+
+class _Child:
+    handle = None
+    _destroy = None
+
+    def _adopt(self, ctx):
+        self.ctx = ctx
+        ctx._children.add(self)
+
+    def close(self):
+        if self.handle:
+            if self.ctx.handle:
+                type(self)._destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
 
 class Context:
     """A device and the CUDA stream the library issues its work on.
@@ -168,12 +213,31 @@ class Context:
         self.handle = handle
         self.device = device
         self._stream = stream
+        self._children = weakref.WeakSet()
+        _live_contexts.add(self)
 
     def synchronize(self):
         _check(_lib.mps_ctx_synchronize(self.handle))
 
     def set_alloc_limit(self, nbytes: int):
         _check(_lib.mps_ctx_set_alloc_limit(self.handle, int(nbytes)))
+
+    def profile(self, kinds=()):
+        """Time every launch of the named kernel classes with CUDA events."""
+        mask = 0
+        for k in kinds:
+            mask |= 1 << KERNEL_KINDS.index(k)
+        _check(_lib.mps_ctx_profile(self.handle, mask))
+
+    def profile_read(self, reset: bool = False) -> dict:
+        """{kind: (launches, timed launches, ms)} since the last reset."""
+        out = {}
+        for i, k in enumerate(KERNEL_KINDS):
+            a, b, ms = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+            _check(_lib.mps_ctx_profile_read(self.handle, i, ctypes.byref(a), ctypes.byref(b), ctypes.byref(ms),
+                                             1 if reset else 0))
+            out[k] = (a.value, b.value, ms.value)
+        return out
 
     def bytes_allocated(self) -> int:
         v = ctypes.c_size_t()
@@ -182,6 +246,8 @@ class Context:
 
     def close(self):
         if self.handle:
+            for child in list(self._children):
+                child.close()
             _lib.mps_ctx_destroy(self.handle)
             self.handle = None
 
@@ -192,9 +258,11 @@ class Context:
             pass
 
 
-class Hamiltonian:
+class Hamiltonian(_Child):
+    _destroy = staticmethod(lambda h: _lib.mps_ham_destroy(h))
+
     def __init__(self, ctx: Context, ham):
-        self.ctx = ctx
+        self._adopt(ctx)
         self.n_qubits = int(ham.n_qubits)
         ops = np.ascontiguousarray(ham.ops, dtype=np.uint8)
         coeffs = np.ascontiguousarray(ham.coeffs, dtype=np.float64)
@@ -209,21 +277,12 @@ class Hamiltonian:
         _check(_lib.mps_hamiltonian_info(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
         return {"n_terms": a.value, "n_nodes": b.value, "max_level_nodes": c.value}
 
-    def close(self):
-        if self.handle:
-            _lib.mps_ham_destroy(self.handle)
-            self.handle = None
 
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
+class Circuit(_Child):
+    _destroy = staticmethod(lambda h: _lib.mps_circuit_destroy(h))
 
-
-class Circuit:
     def __init__(self, ctx: Context, tmpl):
-        self.ctx = ctx
+        self._adopt(ctx)
         self.n_qubits = int(tmpl.n_qubits)
         self.n_params = int(tmpl.n_params)
         self.n_gates = int(tmpl.n_gates)
@@ -233,24 +292,15 @@ class Circuit:
                                        ctypes.byref(h)))
         self.handle = h
 
-    def close(self):
-        if self.handle:
-            _lib.mps_circuit_destroy(self.handle)
-            self.handle = None
 
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
-
-
-class State:
+class State(_Child):
     """A right-canonical MPS on the GPU."""
+
+    _destroy = staticmethod(lambda h: _lib.mps_destroy(h))
 
     def __init__(self, ctx: Context, n_qubits: int, init_bits=None, chi_max: int = 64, precision: str = "fp64",
                  trunc_rel: float = 0.0, svd_fp64: bool = True, svd_max_sweeps: int = 0, svd_tol: float = 0.0):
-        self.ctx = ctx
+        self._adopt(ctx)
         self.n = int(n_qubits)
         self.cfg = Config(int(chi_max), PRECISIONS[precision], float(trunc_rel), 1 if svd_fp64 else 0,
                           int(svd_max_sweeps), float(svd_tol))
@@ -323,17 +373,6 @@ class State:
         rep = Report()
         _check(_lib.mps_get_report(self.handle, ctypes.byref(rep)))
         return rep.as_dict()
-
-    def close(self):
-        if self.handle:
-            _lib.mps_destroy(self.handle)
-            self.handle = None
-
-    def __del__(self):
-        try:
-            self.close()
-        except Exception:
-            pass
 
 
 def vqe_eval(ctx: Context, requests):
