@@ -248,6 +248,8 @@ def run_gpu(args):
     ctx = mps.Context(local, stream=stream)
     H = mps.Hamiltonian(ctx, w["ham"])
     C = mps.Circuit(ctx, w["tmpl"])
+    if args.svd is None:
+        args.svd = "fp64" if w["precision"] == "fp64" else "fp32"
     svd64 = args.svd == "fp64"
     st = mps.State(ctx, w["tmpl"].n_qubits, w["bits"], chi_max=w["chi"], precision=w["precision"],
                    trunc_rel=w["trunc"], svd_fp64=svd64)
@@ -375,10 +377,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c2")
-    ap.add_argument("--excitations", type=int, default=200)
+    ap.add_argument("--excitations", type=int, default=100)
     ap.add_argument("--trunc-rel", type=float, default=1e-5)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default=None)
-    ap.add_argument("--svd", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--svd", choices=["fp32", "fp64"], default=None,
+                    help="Jacobi SVD precision (default: fp64 for complex128 states, fp32 for complex64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
