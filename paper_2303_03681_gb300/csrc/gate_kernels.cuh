@@ -113,8 +113,10 @@ __global__ void __launch_bounds__(kTile* kTile)
         for (int jp = 0; jp < 2; ++jp) cfma(out, ccast<C>(gate->u[(2 * i + j) * 4 + 2 * ip + jp]), acc[ip][jp]);
       const int row = 2 * al + i, col = j * chi_r + ar;
       Cm[(size_t)row * n + col] = out;
-      cplx<S> o = ccast<cplx<S>>(out);
-      A[(size_t)col * m + row] = cmk<S>(S(lam) * o.x, S(lam) * o.y);
+      if (A) {
+        cplx<S> o = ccast<cplx<S>>(out);
+        A[(size_t)col * m + row] = cmk<S>(S(lam) * o.x, S(lam) * o.y);
+      }
     }
   }
 }

@@ -5,6 +5,7 @@
 
 #include "gate_kernels.cuh"
 #include "internal.h"
+#include "svd_cluster.cuh"
 
 namespace mpsv {
 
@@ -135,16 +136,89 @@ template <typename S, typename R> static void svd_set_attr() {
   });
 }
 
+// Cluster size for the Jacobi SVD of a theta with up to mcap columns of
+// A = C~^H and ncap rows, or 0 when the single-CTA kernel is used.
+template <typename S, typename R> static int cluster_svd_size(int mcap, int ncap) {
+  if (mcap < 96) return 0;
+  static int max16 = -1;
+  static std::once_flag f;
+  std::call_once(f, [] {
+    cudaFuncSetAttribute(svd_cluster_kernel<S, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(max_dyn_smem() - 1024));
+    cudaFuncSetAttribute(svd_cluster_kernel<S, R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = max_dyn_smem() - 2048;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, svd_cluster_kernel<S, R>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      n = 0;
+    }
+    max16 = n;
+  });
+  for (int P = (mcap >= 192 && max16 > 0) ? 16 : 8; P <= 16; P *= 2) {
+    if (P == 16 && max16 <= 0) break;
+    const int b = (mcap + 2 * P - 1) / (2 * P);
+    ClusterSvdSmem<S> L(b, ncap, 2 * P * b, 512);
+    if (L.total + 2048 <= max_dyn_smem()) return P;
+  }
+  return 0;
+}
+
 template <typename R, typename S>
 static void launch_two_qubit(mps_state* st, const DevGate* g, int q, cudaStream_t s) {
   const int cap_l = st->cap[q], cap_m = st->cap[q + 1], cap_r = st->cap[q + 2];
   const dim3 blk(kTile, kTile);
   const dim3 g1((cap_r + kTile - 1) / kTile, (cap_l + kTile - 1) / kTile);
+  const int P = cluster_svd_size<S, R>(2 * cap_l, 2 * cap_r);
   {
     KernelScope k(st->ctx, MPS_K_THETA);
     theta_kernel<R, S><<<g1, blk, 0, s>>>(site_ptr<R>(st, q), site_ptr<R>(st, q + 1), g,
                                           st->d_lam + st->lam_off[q], st->d_chi, q,
-                                          reinterpret_cast<cplx<R>*>(st->d_C), reinterpret_cast<cplx<S>*>(st->d_A));
+                                          reinterpret_cast<cplx<R>*>(st->d_C),
+                                          P ? nullptr : reinterpret_cast<cplx<S>*>(st->d_A));
+  }
+  SvdParams p;
+  p.chi_max = st->cfg.chi_max;
+  p.max_sweeps = st->cfg.svd_max_sweeps > 0 ? st->cfg.svd_max_sweeps : 60;
+  p.trunc_rel = st->cfg.trunc_rel;
+  p.tol = st->cfg.svd_tol;
+  const dim3 g3((cap_m + kTile - 1) / kTile, (2 * cap_l + kTile - 1) / kTile);
+  if (P) {
+    const int b = (2 * cap_l + 2 * P - 1) / (2 * P);
+    ClusterSvdSmem<S> L(b, 2 * cap_r, 2 * P * b, 512);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(P);
+    cfg.blockDim = dim3(512);
+    cfg.dynamicSmemBytes = L.total;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = P;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    {
+      KernelScope k(st->ctx, MPS_K_SVD);
+      cudaLaunchKernelEx(&cfg, svd_cluster_kernel<S, R>, (const cplx<R>*)reinterpret_cast<cplx<R>*>(st->d_C),
+                         (const double*)(st->d_lam + st->lam_off[q]), st->d_chi, q, p, site_ptr<R>(st, q + 1),
+                         st->d_lam + st->lam_off[q + 1], st->d_rep);
+    }
+    {
+      KernelScope k(st->ctx, MPS_K_G3);
+      g3_kernel<R><<<g3, blk, 0, s>>>(reinterpret_cast<cplx<R>*>(st->d_C), site_ptr<R>(st, q + 1), st->d_chi, q,
+                                      st->d_rep, site_ptr<R>(st, q));
+    }
+    return;
   }
   const int mcap = 2 * cap_l, ncap = 2 * cap_r;
   const size_t full = svd_smem_bytes<S>(mcap, ncap, true);
@@ -152,18 +226,12 @@ static void launch_two_qubit(mps_state* st, const DevGate* g, int q, cudaStream_
   const size_t smem = svd_smem_bytes<S>(mcap, ncap, use_smem);
   svd_set_attr<S, R>();
   int warps = std::min(32, std::max(1, ncap / 2));
-  SvdParams p;
-  p.chi_max = st->cfg.chi_max;
-  p.max_sweeps = st->cfg.svd_max_sweeps > 0 ? st->cfg.svd_max_sweeps : 60;
-  p.trunc_rel = st->cfg.trunc_rel;
-  p.tol = st->cfg.svd_tol;
   {
     KernelScope k(st->ctx, MPS_K_SVD);
     svd_truncate_kernel<S, R><<<1, 32 * warps, smem, s>>>(
         reinterpret_cast<cplx<S>*>(st->d_A), reinterpret_cast<cplx<S>*>(st->d_V), use_smem ? 1 : 0, st->d_chi, q,
         p, site_ptr<R>(st, q + 1), st->d_lam + st->lam_off[q + 1], st->d_rep);
   }
-  const dim3 g3((cap_m + kTile - 1) / kTile, (2 * cap_l + kTile - 1) / kTile);
   {
     KernelScope k(st->ctx, MPS_K_G3);
     g3_kernel<R><<<g3, blk, 0, s>>>(reinterpret_cast<cplx<R>*>(st->d_C), site_ptr<R>(st, q + 1), st->d_chi, q,

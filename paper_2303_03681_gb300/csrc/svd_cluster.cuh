@@ -1,0 +1,335 @@
+// One-sided Jacobi SVD on a thread-block cluster (Algorithm 1 of the paper's
+// "SVD and one-side jacobi" subsection, parallelised over up to 16 SMs).
+//
+// The kernel orthogonalises the columns of A = C~^H (n_rows = 2 chi_r rows,
+// n_cols = 2 chi_l columns), read from the row-major theta C as
+// A[:, r] = lam_q[r / 2] * conj(C[r, :]).  When the columns are mutually
+// orthogonal, A = W Sigma with W the right singular vectors of C~, so the
+// kept rows of B~_{q+1} = W^H are the conjugated, normalised columns and no
+// rotation accumulator is needed.
+//
+// Parallel order.  The n_cols columns are split into 2P blocks of b columns
+// (zero-padded).  CTA p of the P-CTA cluster holds the blocks at positions p
+// and 2P-1-p of a circle-method round robin over the 2P blocks: in each of
+// the 2P-1 rounds of a sweep every CTA orthogonalises all column pairs
+// between its two blocks (and, in the first round, also the pairs inside
+// each block), then every block except the one at position 0 advances one
+// position.  Blocks move through distributed shared memory into ping-pong
+// buffers, so one cluster barrier per round orders the hand-over.
+#pragma once
+
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+
+namespace mpsv {
+
+namespace cg = cooperative_groups;
+
+// Position (0 .. 2P-1) -> (CTA rank, slot 0 = top / 1 = bottom).
+__device__ __forceinline__ void pos_owner(int pos, int P, int& rank, int& slot) {
+  if (pos < P) {
+    rank = pos;
+    slot = 0;
+  } else {
+    rank = 2 * P - 1 - pos;
+    slot = 1;
+  }
+}
+
+template <typename S>
+struct ClusterSvdSmem {
+  // layout of the dynamic shared memory (offsets in bytes)
+  size_t buf, red, sig, rank;
+  size_t total;
+  __host__ __device__ static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+  __host__ __device__ ClusterSvdSmem(int b, int rows, int ncols_pad, int nthreads) {
+    buf = 0;
+    size_t slots = 2ull * 2 * b * rows * sizeof(cplx<S>);  // ping-pong x {top, bottom}
+    red = align16(buf + slots);
+    sig = align16(red + 4ull * (nthreads / 32 + 1) * sizeof(S) * 2);
+    rank = align16(sig + (size_t)ncols_pad * sizeof(double));
+    total = align16(rank + (size_t)ncols_pad * sizeof(int)) + 64;
+  }
+};
+
+template <typename S, typename R>
+__global__ void __launch_bounds__(512, 1)
+    svd_cluster_kernel(const cplx<R>* __restrict__ Cm, const double* __restrict__ lam_l, int* __restrict__ chi, int q,
+                       SvdParams p, cplx<R>* __restrict__ Bnext, double* __restrict__ lam_next,
+                       DevReport* __restrict__ rep) {
+  using C = cplx<S>;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int P = (int)cluster.num_blocks();
+  const int me = (int)cluster.block_rank();
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_flag_in[16];
+  __shared__ int s_k;
+  __shared__ double s_nrm;
+
+  const int chi_l = chi[q], chi_r = chi[q + 2];
+  const int rows = 2 * chi_r;   // length of a column of A = C~^H
+  const int ncols = 2 * chi_l;  // columns to orthogonalise
+  const int b = (ncols + 2 * P - 1) / (2 * P);
+  const int ncols_pad = 2 * P * b;
+  const int nt = blockDim.x;
+  const ClusterSvdSmem<S> L(b, rows, ncols_pad, nt);
+  C* bufs = reinterpret_cast<C*>(smem + L.buf);
+  S* red = reinterpret_cast<S*>(smem + L.red);
+  double* sig = reinterpret_cast<double*>(smem + L.sig);
+  int* rnk = reinterpret_cast<int*>(smem + L.rank);
+  const size_t slot_elems = (size_t)b * rows;
+  auto col_ptr = [&](int pp, int slot, int c) -> C* { return bufs + ((size_t)(pp * 2 + slot) * b + c) * rows; };
+
+  // ---- load: position pos holds the initial block pos (columns pos*b ..)
+  for (int slot = 0; slot < 2; ++slot) {
+    const int pos = slot == 0 ? me : 2 * P - 1 - me;
+    for (size_t t = threadIdx.x; t < slot_elems; t += nt) {
+      const int c = (int)(t / rows), r = (int)(t % rows);
+      const int col = pos * b + c;
+      C v = cmk<S>(0, 0);
+      if (col < ncols) {
+        const cplx<R> x = Cm[(size_t)col * rows + r];
+        const S w = S(lam_l[col >> 1]);
+        v = cmk<S>(w * S(x.x), -w * S(x.y));
+      }
+      col_ptr(0, slot, c)[r] = v;
+    }
+  }
+  // ||A||_F^2: each CTA's share goes to every CTA, summed in rank order
+  __shared__ double s_fro[16];
+  double part = 0.0;
+  for (size_t t = threadIdx.x; t < 2 * slot_elems; t += nt) {
+    const C v = bufs[t];
+    part += double(v.x) * v.x + double(v.y) * v.y;
+  }
+  part = warp_sum(part);
+  if (threadIdx.x == 0) s_nrm = 0.0;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) atomicAdd(&s_nrm, part);
+  __syncthreads();
+  if (threadIdx.x < P) *cluster.map_shared_rank(&s_fro[me], (int)threadIdx.x) = s_nrm;
+  cluster.sync();
+  double fro2 = 0.0;
+  for (int r2 = 0; r2 < P; ++r2) fro2 += s_fro[r2];
+
+  const S eps_u = sizeof(S) == 8 ? S(1.1102230246251565e-16) : S(5.9604645e-08f);
+  const S tol = p.tol > 0 ? S(p.tol) : S(max(rows, ncols)) * eps_u;
+  const S floor = S(double(tol) * double(tol) * fro2);
+  const S tiny = sizeof(S) == 8 ? S(1e-290) : S(1e-35f);
+  // threads per pair: the largest power of two with b groups in the block
+  int T = 1;
+  while (2 * T * b <= nt) T *= 2;
+  const int pair = threadIdx.x / T, lt = threadIdx.x % T;
+  const bool active = pair < b;
+  const int warps_per_pair = (T + 31) / 32;
+  const int width = T < 32 ? T : 32;  // shuffle width (aligned groups of T lanes)
+
+  int sweep = 0, cur = 0;
+  bool converged = false;
+  for (; sweep < p.max_sweeps; ++sweep) {
+    int rotated = 0;
+    for (int round = 0; round < 2 * P - 1; ++round) {
+      const int subrounds = round == 0 ? 2 * b - 1 : b;
+      for (int sr = 0; sr < subrounds; ++sr) {
+        int ci = 0, cj = 0, si = 0, sj = 1;  // column index within slot, slot
+        if (round == 0) {
+          int a0, a1;
+          const int mod = 2 * b - 1;
+          if (pair == 0) {
+            a0 = mod;
+            a1 = sr;
+          } else {
+            a0 = (sr + pair) % mod;
+            a1 = (sr - pair + mod) % mod;
+          }
+          si = a0 / b, ci = a0 % b;
+          sj = a1 / b, cj = a1 % b;
+        } else {
+          si = 0, ci = pair;
+          sj = 1, cj = (pair + sr) % b;
+        }
+        C* ai = col_ptr(cur, si, active ? ci : 0);
+        C* aj = col_ptr(cur, sj, active ? cj : 0);
+        S alpha = 0, beta = 0, gr = 0, gi = 0;
+        for (int r = lt; active && r < rows; r += T) {
+          const C x = ai[r], y = aj[r];
+          alpha = fma(x.x, x.x, fma(x.y, x.y, alpha));
+          beta = fma(y.x, y.x, fma(y.y, y.y, beta));
+          gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+          gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          if (o < width) {
+            alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
+            beta += __shfl_xor_sync(0xffffffffu, beta, o);
+            gr += __shfl_xor_sync(0xffffffffu, gr, o);
+            gi += __shfl_xor_sync(0xffffffffu, gi, o);
+          }
+        }
+        if (warps_per_pair > 1) {
+          const int w = lt / 32;
+          if ((lt & 31) == 0) {
+            S* rr = red + ((size_t)pair * warps_per_pair + w) * 4;
+            rr[0] = alpha;
+            rr[1] = beta;
+            rr[2] = gr;
+            rr[3] = gi;
+          }
+          __syncthreads();
+          alpha = beta = gr = gi = 0;
+          for (int w2 = 0; w2 < warps_per_pair; ++w2) {
+            const S* rr = red + ((size_t)pair * warps_per_pair + w2) * 4;
+            alpha += rr[0];
+            beta += rr[1];
+            gr += rr[2];
+            gi += rr[3];
+          }
+        }
+        const S mag = sqrt(gr * gr + gi * gi);
+        const bool rot =
+            active && (mag > tiny) && (mag > tol * sqrt(alpha * beta)) && (min(alpha, beta) > floor);
+        if (rot) {
+          rotated = 1;
+          const S phr = gr / mag, phi = gi / mag;
+          const S zeta = (beta - alpha) / (S(2) * mag);
+          const S t = (zeta >= S(0) ? S(1) : S(-1)) / (fabs(zeta) + sqrt(S(1) + zeta * zeta));
+          const S c = S(1) / sqrt(S(1) + t * t);
+          const S s = t * c;
+          const C sph = cmk<S>(s * phr, s * phi);
+          for (int r = lt; r < rows; r += T) {
+            const C x = ai[r], y = aj[r];
+            C ni = cmk<S>(c * x.x, c * x.y);
+            ni = csub(ni, cmulc(sph, y));
+            C nj = cmk<S>(c * y.x, c * y.y);
+            nj = cadd(nj, cmul(sph, x));
+            ai[r] = ni;
+            aj[r] = nj;
+          }
+        }
+        __syncthreads();
+      }
+      // ---- hand the blocks on: position pos -> pos + 1 (pos >= 1), 2P-1 -> 1
+      const int nxt = cur ^ 1;
+      for (int slot = 0; slot < 2; ++slot) {
+        const int pos = slot == 0 ? me : 2 * P - 1 - me;
+        int npos = pos == 0 ? 0 : (pos == 2 * P - 1 ? 1 : pos + 1);
+        int drank, dslot;
+        pos_owner(npos, P, drank, dslot);
+        C* src = col_ptr(cur, slot, 0);
+        C* dst = cluster.map_shared_rank(col_ptr(nxt, dslot, 0), drank);
+        for (size_t t = threadIdx.x; t < slot_elems; t += nt) dst[t] = src[t];
+      }
+      cluster.sync();
+      cur = nxt;
+    }
+    // ---- convergence: every CTA tells every CTA whether it rotated
+    __shared__ int s_any;
+    if (threadIdx.x == 0) s_any = 0;
+    __syncthreads();
+    if (rotated) s_any = 1;
+    __syncthreads();
+    if (threadIdx.x < P) {
+      int* dst = cluster.map_shared_rank(s_flag_in, (int)threadIdx.x);
+      dst[me] = s_any;
+    }
+    cluster.sync();
+    int any = 0;
+    for (int r2 = 0; r2 < P; ++r2) any |= s_flag_in[r2];
+    cluster.sync();  // all reads done before the next sweep's writes
+    if (!any) {
+      converged = true;
+      ++sweep;
+      break;
+    }
+  }
+
+  // ---- singular values: column norms, shared with every CTA
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nt >> 5;
+  for (int c = warp; c < 2 * b; c += nw) {
+    const C* a = col_ptr(cur, c / b, c % b);
+    double acc = 0.0;
+    for (int r = lane; r < rows; r += 32) acc += double(a[r].x) * a[r].x + double(a[r].y) * a[r].y;
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      const double sv = sqrt(acc);
+      const int g = me * 2 * b + c;
+      for (int r2 = 0; r2 < P; ++r2) *cluster.map_shared_rank(sig + g, r2) = sv;
+    }
+  }
+  cluster.sync();
+  // ranks (descending, ties by index), the same in every CTA
+  for (int g = threadIdx.x; g < ncols_pad; g += nt) {
+    const double sg = sig[g];
+    int rk = 0;
+    for (int h = 0; h < ncols_pad; ++h) {
+      const double sh = sig[h];
+      rk += (sh > sg) || (sh == sg && h < g);
+    }
+    rnk[g] = rk;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // the sorted values, by scattering through the ranks into red-free scratch:
+    // walk ranks in order using a local search (ncols_pad is small)
+    double total = 0.0, smax = 0.0;
+    for (int g = 0; g < ncols_pad; ++g) {
+      total += sig[g] * sig[g];
+      smax = fmax(smax, sig[g]);
+    }
+    int cnt = 0;
+    for (int g = 0; g < ncols_pad; ++g)
+      if (p.trunc_rel > 0.0 ? (sig[g] > p.trunc_rel * smax) : (sig[g] > 0.0)) ++cnt;
+    int k = min(cnt, min(p.chi_max, min(rows, ncols)));
+    if (k < 1) k = 1;
+    double kept = 0.0, smin = 0.0, s_next = 0.0;
+    for (int g = 0; g < ncols_pad; ++g) {
+      if (rnk[g] < k) kept += sig[g] * sig[g];
+      if (rnk[g] == k - 1) smin = sig[g];
+      if (rnk[g] == k) s_next = sig[g];
+    }
+    double nrm = sqrt(kept);
+    if (!(nrm > 0.0)) nrm = 1.0;
+    s_k = k;
+    s_nrm = nrm;
+    if (me == 0) {
+      rep->discarded_weight += total > 0.0 ? 1.0 - kept / total : 0.0;
+      if (smin / nrm < rep->min_kept_sv) rep->min_kept_sv = smin / nrm;
+      if (k > rep->max_chi) rep->max_chi = k;
+      if (k < ncols && k == p.chi_max && s_next > 0.0 && fabs(smin - s_next) <= 1e-10 * smin)
+        rep->degenerate_cuts += 1;
+      if (!converged) rep->not_converged += 1;
+      const int used = converged ? sweep : p.max_sweeps + 1;
+      if (used > rep->max_sweeps) rep->max_sweeps = used;
+      rep->two_qubit_gates += 1;
+      // per sweep and column pair: three dot products (16 rows flops) and one
+      // rotation of the two columns (12 rows flops)
+      rep->svd_flops += (double)min(used, p.max_sweeps) * 0.5 * ncols * (ncols - 1) * 28.0 * rows;
+      rep->inv_norm = 1.0 / nrm;
+      chi[q + 1] = k;
+    }
+  }
+  __syncthreads();
+  const int k = s_k;
+  const double inv = 1.0 / s_nrm;
+  if (me == 0)
+    for (int g = threadIdx.x; g < ncols_pad; g += nt)
+      if (rnk[g] < k) lam_next[rnk[g]] = sig[g] * inv;
+  // B~_{q+1}[a, :] = conj(A[:, g]) / sigma_g for the column g of rank a < k
+  for (int c = warp; c < 2 * b; c += nw) {
+    const int g = me * 2 * b + c;
+    const int a = rnk[g];
+    if (a >= k) continue;
+    const double sv = sig[g];
+    const S is = sv > 0.0 ? S(1.0 / sv) : S(0);
+    const C* col = col_ptr(cur, c / b, c % b);
+    for (int r = lane; r < rows; r += 32) {
+      const C v = col[r];
+      Bnext[(size_t)a * rows + r] = ccast<cplx<R>>(cmk<S>(v.x * is, -v.y * is));
+    }
+  }
+  cluster.sync();  // no CTA leaves while its shared memory may still be read
+}
+
+}  // namespace mpsv

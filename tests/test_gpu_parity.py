@@ -119,6 +119,31 @@ def test_svd_global_memory_path(mps, ctx):
     assert om.fidelity(got, ref) >= 1 - 1e-10
 
 
+@pytest.mark.parametrize("precision,svd64,chi", [("fp32", False, 48), ("fp32", False, 100), ("fp32", True, 64),
+                                                 ("fp64", True, 128)])
+def test_cluster_svd_path(mps, ctx, precision, svd64, chi):
+    """Thetas with 2 chi_l >= 96 columns take the thread-block-cluster Jacobi
+    (8 CTAs below 192 columns, 16 above); ragged chi pads the column blocks."""
+    n = 16
+    circ = brickwork_circuit(n, 14, make_rng(MASTER_SEED + 12))
+    trunc = 1e-6 if precision == "fp32" else 1e-12
+    ref = om.run_circuit(n, None, circ, chi_max=chi, eps_rel=trunc)
+    st = mps.State(ctx, n, None, chi_max=chi, precision=precision, trunc_rel=trunc, svd_fp64=svd64)
+    rep = st.apply_gates(circ)
+    assert rep["svd_not_converged"] == 0
+    got = to_oracle(st)
+    ham = random_local_pauli_sum(n, 300, make_rng(MASTER_SEED + 13))
+    e = st.energy(mps.Hamiltonian(ctx, ham))
+    if precision == "fp64":
+        assert list(st.bond_dims()) == ref.bond_dims()
+        assert spectra_close(got.lam, ref.lam, 1e-9)
+        assert abs(e - om.energy(ref, ham)) <= 1e-9
+        assert om.fidelity(got, ref) >= 1 - 1e-10
+    else:
+        assert abs(e - om.energy(ref, ham)) <= 2e-5
+        assert om.fidelity(got, ref) >= 1 - 1e-5
+
+
 def test_uccsd_template_through_vqe_eval(mps, ctx):
     n_so, n_e = 10, 4
     rng = make_rng(MASTER_SEED + 6)
