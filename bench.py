@@ -67,6 +67,27 @@ def build_workload(name, args, rank):
     raise SystemExit(f"unknown workload {name}")
 
 
+def max_over_ranks(seconds, dist, device=None):
+    """The job's time: the slowest rank's (barrier-bracketed) timed region."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(seconds)
+    import torch
+
+    t = torch.tensor([float(seconds)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(steps_per_rank, world, seconds):
+    """Whole-job evals/s: every rank evaluates its own instance (weak scaling)."""
+    return world * steps_per_rank / seconds
+
+
+def rank_seed(rank):
+    """Seed of rank r's angles: each rank evaluates a different instance."""
+    return MASTER_SEED + 1000 * (rank + 1)
+
+
 def thetas_for(w, count, seed):
     rng = make_rng(seed)
     n = max(1, w["tmpl"].n_params)
@@ -254,7 +275,7 @@ def run_gpu(args):
     st = mps.State(ctx, w["tmpl"].n_qubits, w["bits"], chi_max=w["chi"], precision=w["precision"],
                    trunc_rel=w["trunc"], svd_fp64=svd64)
     n_steps = args.warmup + args.steps
-    thetas = thetas_for(w, n_steps + args.steps, MASTER_SEED + 1000 * (rank + 1))
+    thetas = thetas_for(w, n_steps + args.steps, rank_seed(rank))
     d_theta = torch.tensor(np.stack(thetas[:n_steps]) if w["tmpl"].n_params else np.zeros((n_steps, 1)),
                            dtype=torch.float64, device=f"cuda:{local}")
     d_energy = torch.zeros(n_steps, dtype=torch.float64, device=f"cuda:{local}")
@@ -291,11 +312,7 @@ def run_gpu(args):
     rep = st.report()  # statistics of the last step only
     svd_flops_last = rep["svd_flops"]
     step_ms = [a.elapsed_time(b) for a, b in events]
-    total_s = sum(step_ms) / 1e3
-    if dist:
-        t = torch.tensor([total_s], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, f"cuda:{local}")
     kprof = ctx.profile_read(reset=True)
     energies = d_energy.cpu().numpy()
 
@@ -309,17 +326,13 @@ def run_gpu(args):
         e, status = mps.vqe_eval(ctx, [(st, C, H, host_thetas[k], w["bits"])])
         e2e_times.append(time.perf_counter() - t0)
         assert status[0] == 0
-    e2e_s = sum(e2e_times)
-    if dist:
-        t = torch.tensor([e2e_s], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(sum(e2e_times), dist, f"cuda:{local}")
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    value = world * args.steps / total_s
+    value = job_throughput(args.steps, world, total_s)
     launches_per_step = sum(v[0] for v in kprof.values()) / args.steps
     dom_launches, dom_timed, dom_ms = kprof[dominant]
     roofline = None
@@ -349,7 +362,7 @@ def run_gpu(args):
         "config": dict(w["desc"], precision=f"{w['precision']} storage/contractions, {args.svd} Jacobi SVD, "
                                             f"FP64 energy sum", l2="flushed between steps (256 MB write)",
                        parallelism=f"replicas x{world}"),
-        "e2e": {"value": world * args.steps / e2e_s, "unit": "evals/s",
+        "e2e": {"value": job_throughput(args.steps, world, e2e_s), "unit": "evals/s",
                 "h2d_bytes_per_step": 8 * w["tmpl"].n_params, "d2h_bytes_per_step": 8},
         "gpu_launches": int(launches_per_step * args.steps),
         "roofline": roofline,

@@ -257,7 +257,8 @@ __global__ void __launch_bounds__(1024, 1)
   }
   __syncthreads();
 
-  const S tol = p.tol > 0 ? S(p.tol) : S(max(m, n)) * SvdEps<S>::unit();
+  // rotate while |b_ij| > tol sqrt(b_ii b_jj), tol = 4 sqrt(max(m, n)) u
+  const S tol = p.tol > 0 ? S(p.tol) : S(4.0 * sqrt(double(max(m, n)))) * SvdEps<S>::unit();
   // ||A||_F^2 sets the noise floor of a column
   {
     double part = 0.0;
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(1024, 1)
     __syncthreads();
   }
   const double fro2 = s_nrm;
-  const S floor = S(double(tol) * double(tol) * fro2);
+  const S floor = S(16.0 * double(SvdEps<S>::unit()) * double(SvdEps<S>::unit()) * fro2);
   __syncthreads();
   const int sweeps = jacobi_sweeps<S>(A, V, m, n, p.max_sweeps, tol, floor, &s_flag);
 

@@ -113,9 +113,15 @@ __global__ void __launch_bounds__(512, 1)
   double fro2 = 0.0;
   for (int r2 = 0; r2 < P; ++r2) fro2 += s_fro[r2];
 
+  // Stopping rule and rounding floor: rotate while |b_ij| > tol sqrt(b_ii b_jj)
+  // with tol = 4 sqrt(max(rows, cols)) u (a few times the rounding error of a
+  // dot product); columns with squared norm below (4 u ||A||_F)^2 are rounding
+  // noise and left alone.  The floor must stay far below any kept singular
+  // value: without a rotation accumulator an unrotated column would become a
+  // non-orthogonal row of B~_{q+1}.
   const S eps_u = sizeof(S) == 8 ? S(1.1102230246251565e-16) : S(5.9604645e-08f);
-  const S tol = p.tol > 0 ? S(p.tol) : S(max(rows, ncols)) * eps_u;
-  const S floor = S(double(tol) * double(tol) * fro2);
+  const S tol = p.tol > 0 ? S(p.tol) : S(4.0 * sqrt(double(max(rows, ncols)))) * eps_u;
+  const S floor = S(16.0 * double(eps_u) * double(eps_u) * fro2);
   const S tiny = sizeof(S) == 8 ? S(1e-290) : S(1e-35f);
   // threads per pair: the largest power of two with b groups in the block
   int T = 1;

@@ -145,7 +145,7 @@ def test_cluster_svd_path(mps, ctx, precision, svd64, chi):
 
 
 def test_uccsd_template_through_vqe_eval(mps, ctx):
-    n_so, n_e = 10, 4
+    n_so, n_e = 8, 4
     rng = make_rng(MASTER_SEED + 6)
     h, g = random_integrals(n_so // 2, rng)
     ham = jw_molecular_hamiltonian(h, g)
