@@ -214,6 +214,45 @@ typedef struct {
 mps_status vqe_eval(mps_ctx* ctx, const vqe_request* reqs, size_t n, double* energies_out,
                     mps_status* status_out);
 
+/* Apply one two-qubit gate to two adjacent site tensors that live in the
+ * caller's device memory, allocating nothing.
+ *
+ * The paper has no counterpart to this call.  It exists for callers that
+ * cannot allocate device memory: code running in a CUDA host callback or a
+ * stream-ordered host function (where allocating CUDA calls are not allowed),
+ * embedders that give the library a fixed, pre-partitioned share of device
+ * memory, and processes whose memory budget was fixed at start-up.  The
+ * gate's scratch (theta, the Jacobi matrices, the bond dimensions and the
+ * truncation report) lives in one fixed array of 197,632 bytes compiled into
+ * the library, which every GPU that loads the library keeps until the
+ * process exits.
+ *
+ * Arguments (device pointers unless noted; complex128 as (re, im) doubles):
+ *   device, cuda_stream  the device whose memory the pointers refer to and
+ *                        the stream to issue on (NULL = legacy default);
+ *   chi_l, chi_m, chi_r  current bond dimensions left of site q, between q
+ *                        and q+1, right of q+1; chi_l, chi_r <= 32 and
+ *                        chi_m <= 64 (larger sizes fail with MPS_EINVAL);
+ *   B_left   [chi_l][2][chi_m] on entry, [chi_l][2][k] on return; room for
+ *            chi_l*2*max(chi_m, kmax) entries, kmax = min(chi_max, 2 chi_l, 2 chi_r);
+ *   B_right  [chi_m][2][chi_r] on entry, [k][2][chi_r] on return; room for
+ *            max(chi_m, kmax)*2*chi_r entries;
+ *   lam_left chi_l singular values of the bond left of site q;
+ *   lam_out  receives the k new singular values (room for kmax);
+ *   gate     host array, 4x4 row-major complex (32 doubles), index 2 i_q + i_{q+1};
+ *   chi_max, trunc_rel  truncation as in mps_config;
+ *   chi_out  receives k (one int32).
+ * The update is the one mps_apply_gates makes for a complex128 state.  The
+ * call returns after issuing the work; synchronise the stream before reading
+ * the outputs.  The first call on each device sets the library up for that
+ * device (it looks up the scratch array's device address); make it before
+ * any stream capture.  All calls share the scratch array and it keeps the
+ * last call's contents (the kernels overwrite what they read): calls whose
+ * work overlaps on the GPU, from several streams or threads, race on it. */
+mps_status mps_gate2_noalloc(int device, void* cuda_stream, int32_t chi_l, int32_t chi_m, int32_t chi_r,
+                             double* B_left, double* B_right, const double* lam_left, double* lam_out,
+                             const double* gate, int32_t chi_max, double trunc_rel, int32_t* chi_out);
+
 #ifdef __cplusplus
 }
 #endif
