@@ -257,44 +257,62 @@ def run_gpu(args):
     if world != args.gpus:
         raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
     torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     dist = None
     if world > 1:
         import torch.distributed as dist
 
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        dist.init_process_group("nccl", device_id=dev)
     from paper_2303_03681_gb300 import mps
 
     w = build_workload(args.workload, args, rank)
-    stream = torch.cuda.current_stream()
-    ctx = mps.Context(local, stream=stream)
-    H = mps.Hamiltonian(ctx, w["ham"])
-    C = mps.Circuit(ctx, w["tmpl"])
     if args.svd is None:
         args.svd = "fp64" if w["precision"] == "fp64" else "fp32"
     svd64 = args.svd == "fp64"
-    st = mps.State(ctx, w["tmpl"].n_qubits, w["bits"], chi_max=w["chi"], precision=w["precision"],
-                   trunc_rel=w["trunc"], svd_fp64=svd64)
+    B = args.batch
+    main_stream = torch.cuda.current_stream()
+    streams = [torch.cuda.Stream(device=dev) for _ in range(B)]
+    ctxs = [mps.Context(local, stream=s) for s in streams]
+    H = mps.Hamiltonian(ctxs[0], w["ham"])
+    C = mps.Circuit(ctxs[0], w["tmpl"])
+    states = [mps.State(c, w["tmpl"].n_qubits, w["bits"], chi_max=w["chi"], precision=w["precision"],
+                        trunc_rel=w["trunc"], svd_fp64=svd64) for c in ctxs]
     n_steps = args.warmup + args.steps
-    thetas = thetas_for(w, n_steps + args.steps, rank_seed(rank))
-    d_theta = torch.tensor(np.stack(thetas[:n_steps]) if w["tmpl"].n_params else np.zeros((n_steps, 1)),
-                           dtype=torch.float64, device=f"cuda:{local}")
-    d_energy = torch.zeros(n_steps, dtype=torch.float64, device=f"cuda:{local}")
-    flush = torch.empty(64 << 20, dtype=torch.float32, device=f"cuda:{local}")  # 256 MB > 129 MB L2
+    n_par = max(1, w["tmpl"].n_params)
+    thetas = thetas_for(w, (n_steps + args.steps) * B, rank_seed(rank))
+    th_dev = np.zeros((n_steps, B, n_par))
+    for i in range(n_steps):
+        for b in range(B):
+            th_dev[i, b, :w["tmpl"].n_params] = thetas[i * B + b]
+    d_theta = torch.tensor(th_dev, dtype=torch.float64, device=dev)
+    d_energy = torch.zeros((n_steps, B), dtype=torch.float64, device=dev)
+    flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    def fork_join(fn):
+        go = torch.cuda.Event()
+        go.record(main_stream)
+        for s in streams:
+            s.wait_event(go)
+        fn()
+        for s in streams:
+            done = torch.cuda.Event()
+            done.record(s)
+            main_stream.wait_event(done)
 
     def step(i):
-        st.reset(w["bits"])
-        st.apply_circuit(C, None, device_ptr=d_theta[i].data_ptr())
-        st.energy_async(H, d_energy[i:i + 1].data_ptr())
+        reqs = [(states[b], C, H, d_theta[i, b].data_ptr(), w["bits"]) for b in range(B)]
+        fork_join(lambda: mps.vqe_eval_batch_async(reqs, d_energy[i].data_ptr()))
 
-    ctx.profile(mps.KERNEL_KINDS)
+    for c in ctxs:
+        c.profile(mps.KERNEL_KINDS)
     for i in range(args.warmup):
         flush.zero_()
         step(i)
     torch.cuda.synchronize()
-    prof = ctx.profile_read(reset=True)
+    prof = merge_profiles([c.profile_read(reset=True) for c in ctxs])
     dominant = max(prof, key=lambda k: prof[k][2])
-    ctx.profile([dominant])
-    st.reset(w["bits"])
+    for c in ctxs:
+        c.profile([dominant])
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -304,36 +322,36 @@ def run_gpu(args):
         wall0 = time.perf_counter()
         for k in range(args.steps):
             flush.zero_()  # L2 flush between timed steps, outside the events
-            events[k][0].record(stream)
+            events[k][0].record(main_stream)
             step(args.warmup + k)
-            events[k][1].record(stream)
+            events[k][1].record(main_stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
-    rep = st.report()  # statistics of the last step only
-    svd_flops_last = rep["svd_flops"]
+    reps = [s.report() for s in states]  # statistics of the last step
     step_ms = [a.elapsed_time(b) for a, b in events]
-    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, f"cuda:{local}")
-    kprof = ctx.profile_read(reset=True)
+    total_s = max_over_ranks(sum(step_ms) / 1e3, dist, dev)
+    kprof = merge_profiles([c.profile_read(reset=True) for c in ctxs])
     energies = d_energy.cpu().numpy()
+    hbm_bytes = sum(c.bytes_allocated() for c in ctxs)
 
-    # end to end through the C-ABI with host buffers: theta H2D, energy D2H
+    # end to end through the C-ABI with host buffers: theta H2D, energies D2H
     e2e_times = []
-    host_thetas = thetas[n_steps:n_steps + args.steps]
+    host_thetas = thetas[n_steps * B:]
     for k in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        e, status = mps.vqe_eval(ctx, [(st, C, H, host_thetas[k], w["bits"])])
+        e, status = mps.vqe_eval_batch([(states[b], C, H, host_thetas[k * B + b], w["bits"]) for b in range(B)])
         e2e_times.append(time.perf_counter() - t0)
-        assert status[0] == 0
-    e2e_s = max_over_ranks(sum(e2e_times), dist, f"cuda:{local}")
+        assert all(s == 0 for s in status), status
+    e2e_s = max_over_ranks(sum(e2e_times), dist, dev)
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    value = job_throughput(args.steps, world, total_s)
-    launches_per_step = sum(v[0] for v in kprof.values()) / args.steps
+    value = job_throughput(args.steps * B, world, total_s)
+    launches_total = sum(v[0] for v in kprof.values())
     dom_launches, dom_timed, dom_ms = kprof[dominant]
     roofline = None
     if dom_timed:
@@ -341,16 +359,17 @@ def run_gpu(args):
         per_step = dom_timed / args.steps
         if dominant == "svd":
             dt = "f64" if svd64 else "f32"
-            flops = svd_flops_last / max(per_step, 1)
-            achieved = flops / avg_s / 1e12
+            flops_per_launch = sum(r["svd_flops"] for r in reps) / max(1, sum(r["two_qubit_gates"] for r in reps))
+            achieved = flops_per_launch / avg_s / 1e12
             peak = ALU_PEAK_TFLOPS[dt]
-            roofline = {"bound": "alu", "kernel": "svd_truncate_kernel", "achieved": achieved, "peak": peak,
-                        "unit": "TFLOP/s", "frac": achieved / peak, "traffic": recorded_traffic(dominant,
-                                                                                                 w["desc"]["workload"]),
+            roofline = {"bound": "alu", "kernel": "svd (Jacobi, cluster or single CTA)", "achieved": achieved,
+                        "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                        "traffic": recorded_traffic(dominant, w["desc"]["workload"]),
                         "avg_launch_us": avg_s * 1e6, "launches_per_step": per_step,
                         "peak_source": f"derived {dt.upper()} ALU peak: {SM_COUNT} SMs x "
                                        f"{'128' if dt == 'f32' else '2'} FMA/clk x {SM_MHZ:.0f} MHz",
-                        "work": "Jacobi flops actually run (sweeps x pairs x (16m + 12(m+n))) / launch"}
+                        "work": "Jacobi flops run (sweeps x pairs x per-pair dot and rotation flops) per launch",
+                        "aggregate_achieved": flops_per_launch * per_step / (total_s / args.steps) / 1e12}
         else:
             roofline = {"bound": "alu", "kernel": dominant, "achieved": None, "peak": None, "unit": "TFLOP/s",
                         "frac": None, "traffic": None, "avg_launch_us": avg_s * 1e6, "launches_per_step": per_step}
@@ -360,18 +379,21 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "c64" if w["precision"] == "fp32" else "c128",
         "data": "synthetic",
         "config": dict(w["desc"], precision=f"{w['precision']} storage/contractions, {args.svd} Jacobi SVD, "
-                                            f"FP64 energy sum", l2="flushed between steps (256 MB write)",
-                       parallelism=f"replicas x{world}"),
-        "e2e": {"value": job_throughput(args.steps, world, e2e_s), "unit": "evals/s",
-                "h2d_bytes_per_step": 8 * w["tmpl"].n_params, "d2h_bytes_per_step": 8},
-        "gpu_launches": int(launches_per_step * args.steps),
+                                            f"FP64 energy sum",
+                       batch=f"{B} concurrent evaluations per step (one stream each)",
+                       l2="flushed between steps (256 MB write)", parallelism=f"replicas x{world}"),
+        "e2e": {"value": job_throughput(args.steps * B, world, e2e_s), "unit": "evals/s",
+                "h2d_bytes_per_step": 8 * w["tmpl"].n_params * B, "d2h_bytes_per_step": 8 * B},
+        "gpu_launches": int(launches_total),
         "roofline": roofline,
         "clocks": clocks.summary(),
         "kernel_time_share": {k: round(v[2] / max(1e-9, sum(x[2] for x in prof.values())), 4)
                               for k, v in prof.items() if v[2] > 0},
-        "energies": [float(x) for x in energies[args.warmup:args.warmup + 3]],
-        "last_step_report": {k: rep[k] for k in ("max_chi", "discarded_weight", "svd_not_converged",
-                                                   "degenerate_cuts", "two_qubit_gates")},
+        "energies": [float(x) for x in energies[args.warmup, :min(B, 4)]],
+        "last_step_report": {k: max(r[k] for r in reps) for k in ("max_chi", "discarded_weight", "svd_not_converged",
+                                                                  "degenerate_cuts", "two_qubit_gates",
+                                                                  "max_sweeps_used")},
+        "hbm_bytes_allocated": hbm_bytes,
         "wall_s_timed_region": wall,
     }
     if world == 1 and not args.no_cpu_baseline:
@@ -381,6 +403,15 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def merge_profiles(profs):
+    out = {}
+    for p in profs:
+        for k, (a, b, ms) in p.items():
+            x = out.get(k, (0, 0, 0.0))
+            out[k] = (x[0] + a, x[1] + b, x[2] + ms)
+    return out
 
 
 def main():
@@ -396,6 +427,7 @@ def main():
     ap.add_argument("--svd", choices=["fp32", "fp64"], default=None,
                     help="Jacobi SVD precision (default: fp64 for complex128 states, fp32 for complex64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=1, help="concurrent evaluations per step")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

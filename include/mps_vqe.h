@@ -214,6 +214,20 @@ typedef struct {
 mps_status vqe_eval(mps_ctx* ctx, const vqe_request* reqs, size_t n, double* energies_out,
                     mps_status* status_out);
 
+/* Batched form of vqe_eval (the paper's fragment-level parallelism, L298,
+ * on one GPU): the requests may belong to different contexts, each with its
+ * own stream, and must use distinct states.  The library issues their gates
+ * round-robin (gate g of every request before gate g+1), so independent
+ * evaluations overlap on the device; then it evaluates each energy.
+ * energies_out[i] / status_out[i] (host, status nullable) as in vqe_eval;
+ * the return value is the first failing status, or MPS_OK. */
+mps_status vqe_eval_batch(const vqe_request* reqs, size_t n, double* energies_out, mps_status* status_out);
+/* Same with device-resident data: every request's theta is a device pointer
+ * and d_energies_out is a device array of n doubles.  The call returns once
+ * all work is issued (each energy reads its state's bond dimensions, which
+ * waits for that state's circuit); synchronise the streams before reading. */
+mps_status vqe_eval_batch_async(const vqe_request* reqs, size_t n, double* d_energies_out, mps_status* status_out);
+
 /* Apply one two-qubit gate to two adjacent site tensors that live in the
  * caller's device memory, allocating nothing.
  *

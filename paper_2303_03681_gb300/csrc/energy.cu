@@ -127,7 +127,7 @@ static mps_status build_trie(mps_ham* h, const uint8_t* ops, const double* coeff
 // Environment buffers sized for the bond dimensions the state has now
 // (grow-only); slot strides follow the same dimensions.
 template <typename R>
-static mps_status ensure_env_buffers(const std::vector<int>& chi, mps_ham* h) {
+static mps_status ensure_env_buffers(const std::vector<int>& chi, mps_state* st, const mps_ham* h) {
   size_t Lneed = 16, Mneed = 16;
   for (int j = 0; j < h->n; ++j) {
     const LevelHost& L = h->levels[j];
@@ -135,24 +135,36 @@ static mps_status ensure_env_buffers(const std::vector<int>& chi, mps_ham* h) {
     Lneed = std::max(Lneed, (size_t)L.n_children * cr * cr * sizeof(cplx<R>));
     Mneed = std::max(Mneed, (size_t)L.n_parents * 2 * cl * cr * sizeof(cplx<R>));
   }
-  mps_ctx* c = h->ctx;
-  if (Lneed > h->L_bytes) {
-    dev_free(c, h->d_L[0]);
-    dev_free(c, h->d_L[1]);
-    h->d_L[0] = h->d_L[1] = nullptr;
-    h->L_bytes = 0;
-    mps_status rc = dev_alloc(c, &h->d_L[0], Lneed);
-    if (rc == MPS_OK) rc = dev_alloc(c, &h->d_L[1], Lneed);
+  mps_ctx* c = st->ctx;
+  if (Lneed > st->L_bytes) {
+    dev_free(c, st->d_L[0]);
+    dev_free(c, st->d_L[1]);
+    st->d_L[0] = st->d_L[1] = nullptr;
+    st->L_bytes = 0;
+    mps_status rc = dev_alloc(c, &st->d_L[0], Lneed);
+    if (rc == MPS_OK) rc = dev_alloc(c, &st->d_L[1], Lneed);
     if (rc != MPS_OK) return rc;
-    h->L_bytes = Lneed;
+    st->L_bytes = Lneed;
   }
-  if (Mneed > h->M_bytes) {
-    dev_free(c, h->d_M);
-    h->d_M = nullptr;
-    h->M_bytes = 0;
-    mps_status rc = dev_alloc(c, &h->d_M, Mneed);
+  if (Mneed > st->M_bytes) {
+    dev_free(c, st->d_M);
+    st->d_M = nullptr;
+    st->M_bytes = 0;
+    mps_status rc = dev_alloc(c, &st->d_M, Mneed);
     if (rc != MPS_OK) return rc;
-    h->M_bytes = Mneed;
+    st->M_bytes = Mneed;
+  }
+  if ((size_t)h->n_terms > st->vals_cap || !st->d_vals) {
+    dev_free(c, st->d_vals);
+    st->d_vals = nullptr;
+    st->vals_cap = 0;
+    mps_status rc = dev_alloc(c, (void**)&st->d_vals, std::max<size_t>(16, h->n_terms * sizeof(double)));
+    if (rc != MPS_OK) return rc;
+    st->vals_cap = h->n_terms;
+  }
+  if (!st->d_energy) {
+    mps_status rc = dev_alloc(c, (void**)&st->d_energy, sizeof(double));
+    if (rc != MPS_OK) return rc;
   }
   return MPS_OK;
 }
@@ -171,18 +183,18 @@ static mps_status energy_levels(mps_state* st, mps_ham* h, double* d_out) {
       return MPS_ESTATE;
     }
   }
-  mps_status rc = ensure_env_buffers<R>(chi, h);
+  mps_status rc = ensure_env_buffers<R>(chi, st, h);
   if (rc != MPS_OK) return rc;
   const long long nt = h->n_terms;
   mps_ctx* c = st->ctx;
   if (nt) {
     KernelScope k(c, MPS_K_SETUP);
-    fill_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(h->d_vals, nt, 1.0);
+    fill_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(st->d_vals, nt, 1.0);
   }
   const cplx<R>* B = reinterpret_cast<const cplx<R>*>(st->d_B);
-  cplx<R>* Lprev = reinterpret_cast<cplx<R>*>(h->d_L[0]);
-  cplx<R>* Lcur = reinterpret_cast<cplx<R>*>(h->d_L[1]);
-  cplx<R>* M = reinterpret_cast<cplx<R>*>(h->d_M);
+  cplx<R>* Lprev = reinterpret_cast<cplx<R>*>(st->d_L[0]);
+  cplx<R>* Lcur = reinterpret_cast<cplx<R>*>(st->d_L[1]);
+  cplx<R>* M = reinterpret_cast<cplx<R>*>(st->d_M);
   const dim3 blk(kTile, kTile);
   for (int j = 0; j < h->n; ++j) {
     const LevelHost& L = h->levels[j];
@@ -212,25 +224,26 @@ static mps_status energy_levels(mps_state* st, mps_ham* h, double* d_out) {
     }
     if (L.n_leaves) {
       KernelScope k(c, MPS_K_ENV_LEAF);
-      env_leaf_kernel<R><<<(L.n_leaves + 7) / 8, 256, 0, s>>>(M, Bj, st->d_chi, lv, h->d_vals);
+      env_leaf_kernel<R><<<(L.n_leaves + 7) / 8, 256, 0, s>>>(M, Bj, st->d_chi, lv, st->d_vals);
     }
     if (L.n_traces) {
       KernelScope k(c, MPS_K_ENV_TRACE);
-      env_trace_kernel<R><<<(L.n_traces + 7) / 8, 256, 0, s>>>(Lcur, st->d_chi, lv, h->d_vals);
+      env_trace_kernel<R><<<(L.n_traces + 7) / 8, 256, 0, s>>>(Lcur, st->d_chi, lv, st->d_vals);
     }
     if (L.n_children) std::swap(Lprev, Lcur);
   }
   {
     KernelScope k(c, MPS_K_REDUCE);
-    energy_reduce_kernel<<<1, 1024, 0, s>>>(h->d_vals, h->d_coeffs, nt, 0.0, d_out);
+    energy_reduce_kernel<<<1, 1024, 0, s>>>(st->d_vals, h->d_coeffs, nt, 0.0, d_out ? d_out : st->d_energy);
   }
   MPSV_CUDA(cudaGetLastError());
   return MPS_OK;
 }
 
 mps_status ham_energy_async(mps_state* st, mps_ham* h, double* d_out) {
-  if (h->n != st->n || h->ctx != st->ctx) {
-    set_error("energy: Hamiltonian on %d qubits / another context, state has %d", h->n, st->n);
+  if (h->n != st->n || h->ctx->device != st->ctx->device) {
+    set_error("energy: Hamiltonian on %d qubits (device %d), state has %d (device %d)", h->n, h->ctx->device, st->n,
+              st->ctx->device);
     return MPS_EINVAL;
   }
   if (st->broken) {
@@ -246,7 +259,7 @@ static void destroy_ham(mps_ham* h) {
   DeviceGuard guard(c->device);
   cudaStreamSynchronize(c->stream);
   for (void* p : {(void*)h->d_parent_src, (void*)h->d_child, (void*)h->d_leaf, (void*)h->d_trace,
-                  (void*)h->d_coeffs, (void*)h->d_vals, (void*)h->d_energy, h->d_L[0], h->d_L[1], h->d_M})
+                  (void*)h->d_coeffs})
     dev_free(c, p);
   delete h;
 }
@@ -295,8 +308,6 @@ mps_status mps_hamiltonian_create(mps_ctx* ctx, int32_t n_qubits, size_t n_terms
   up((void**)&h->d_leaf, leaf.data(), leaf.size() * sizeof(int4));
   up((void**)&h->d_trace, trace.data(), trace.size() * sizeof(int2));
   up((void**)&h->d_coeffs, coeffs, n_terms * sizeof(double));
-  if (rc == MPS_OK) rc = dev_alloc(ctx, (void**)&h->d_vals, std::max<size_t>(16, n_terms * sizeof(double)));
-  if (rc == MPS_OK) rc = dev_alloc(ctx, (void**)&h->d_energy, sizeof(double));
   if (rc == MPS_OK) {
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
     if (e != cudaSuccess) rc = cuda_fail(e, "mps_hamiltonian_create");
@@ -338,9 +349,9 @@ mps_status mps_energy(mps_state* st, const mps_ham* h, double* energy_out, doubl
   }
   DeviceGuard guard(st->ctx->device);
   mps_ham* hh = const_cast<mps_ham*>(h);
-  mps_status rc = ham_energy_async(st, hh, hh->d_energy);
+  mps_status rc = ham_energy_async(st, hh, nullptr);
   if (rc != MPS_OK) return rc;
-  MPSV_CUDA(cudaMemcpyAsync(energy_out, hh->d_energy, sizeof(double), cudaMemcpyDeviceToHost, st->ctx->stream));
+  MPSV_CUDA(cudaMemcpyAsync(energy_out, st->d_energy, sizeof(double), cudaMemcpyDeviceToHost, st->ctx->stream));
   if (norm_out) {
     // sum of lam^2 on bond 1 (the first inner bond; bond 0 is the trivial edge)
     const int b = st->n > 1 ? 1 : 0;
@@ -367,10 +378,10 @@ mps_status mps_expectations(mps_state* st, const mps_ham* h, double* values_out)
   }
   DeviceGuard guard(st->ctx->device);
   mps_ham* hh = const_cast<mps_ham*>(h);
-  mps_status rc = ham_energy_async(st, hh, hh->d_energy);
+  mps_status rc = ham_energy_async(st, hh, nullptr);
   if (rc != MPS_OK) return rc;
   if (h->n_terms)
-    MPSV_CUDA(cudaMemcpyAsync(values_out, hh->d_vals, h->n_terms * sizeof(double), cudaMemcpyDeviceToHost,
+    MPSV_CUDA(cudaMemcpyAsync(values_out, st->d_vals, h->n_terms * sizeof(double), cudaMemcpyDeviceToHost,
                               st->ctx->stream));
   MPSV_CUDA(cudaStreamSynchronize(st->ctx->stream));
   return MPS_OK;
@@ -393,9 +404,9 @@ mps_status vqe_eval(mps_ctx* ctx, const vqe_request* reqs, size_t n, double* ene
     }
     if (rc == MPS_OK) rc = state_reset(r.state, r.init_bits);
     if (rc == MPS_OK) rc = mps_apply_circuit_async(r.state, r.circuit, r.theta, 0);
-    if (rc == MPS_OK) rc = ham_energy_async(r.state, const_cast<mps_ham*>(r.ham), r.ham->d_energy);
+    if (rc == MPS_OK) rc = ham_energy_async(r.state, const_cast<mps_ham*>(r.ham), nullptr);
     if (rc == MPS_OK) {
-      cudaError_t e = cudaMemcpyAsync(&energies_out[i], r.ham->d_energy, sizeof(double), cudaMemcpyDeviceToHost,
+      cudaError_t e = cudaMemcpyAsync(&energies_out[i], r.state->d_energy, sizeof(double), cudaMemcpyDeviceToHost,
                                       ctx->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
       if (e != cudaSuccess) rc = cuda_fail(e, "vqe_eval");
@@ -407,6 +418,98 @@ mps_status vqe_eval(mps_ctx* ctx, const vqe_request* reqs, size_t n, double* ene
     if (status_out) status_out[i] = rc;
   }
   return first_bad;
+}
+
+}  // extern "C"
+
+namespace mpsv {
+
+// Shared body of vqe_eval_batch (host theta and energies, synchronising) and
+// vqe_eval_batch_async (device theta and energies).
+static mps_status run_batch(const vqe_request* reqs, size_t n, double* energies_out, mps_status* status_out,
+                            bool on_device) {
+  if (n && (!reqs || !energies_out)) {
+    set_error("vqe_eval_batch: NULL argument");
+    return MPS_EINVAL;
+  }
+  std::vector<mps_status> rc(n, MPS_OK);
+  for (size_t i = 0; i < n; ++i) {
+    const vqe_request& r = reqs[i];
+    if (!r.state || !r.circuit || !r.ham || (!r.theta && r.circuit->n_params)) {
+      set_error("vqe_eval_batch: request %zu has a NULL handle", i);
+      rc[i] = MPS_EINVAL;
+      continue;
+    }
+    for (size_t j = 0; j < i; ++j)
+      if (reqs[j].state == r.state) {
+        set_error("vqe_eval_batch: requests %zu and %zu share a state", j, i);
+        rc[i] = MPS_EINVAL;
+      }
+    if (rc[i] == MPS_OK && (r.circuit->n != r.state->n || r.ham->n != r.state->n ||
+                            r.circuit->ctx->device != r.state->ctx->device)) {
+      set_error("vqe_eval_batch: request %zu mixes sizes or devices", i);
+      rc[i] = MPS_EINVAL;
+    }
+  }
+  // reset + bind on every request's own stream
+  for (size_t i = 0; i < n; ++i) {
+    if (rc[i] != MPS_OK) continue;
+    const vqe_request& r = reqs[i];
+    DeviceGuard guard(r.state->ctx->device);
+    rc[i] = state_reset(r.state, r.init_bits);
+    if (rc[i] == MPS_OK) rc[i] = state_bind_circuit(r.state, r.circuit, r.theta, on_device ? 1 : 0);
+  }
+  // gates round-robin across requests
+  int max_gates = 0;
+  for (size_t i = 0; i < n; ++i)
+    if (rc[i] == MPS_OK) max_gates = std::max(max_gates, reqs[i].circuit->n_gates);
+  for (int g = 0; g < max_gates; ++g) {
+    for (size_t i = 0; i < n; ++i) {
+      const vqe_request& r = reqs[i];
+      if (rc[i] != MPS_OK || g >= r.circuit->n_gates) continue;
+      DeviceGuard guard(r.state->ctx->device);
+      rc[i] = state_apply_device_gates(r.state, r.state->d_bound + g, &r.circuit->q[g], &r.circuit->arity[g], 1);
+      if (rc[i] != MPS_OK) r.state->broken = true;
+    }
+  }
+  // energies (each reads its bond dimensions once), then the results
+  for (size_t i = 0; i < n; ++i) {
+    if (rc[i] != MPS_OK) continue;
+    const vqe_request& r = reqs[i];
+    DeviceGuard guard(r.state->ctx->device);
+    rc[i] = ham_energy_async(r.state, const_cast<mps_ham*>(r.ham), on_device ? energies_out + i : nullptr);
+    if (rc[i] == MPS_OK && !on_device) {
+      cudaError_t e = cudaMemcpyAsync(&energies_out[i], r.state->d_energy, sizeof(double), cudaMemcpyDeviceToHost,
+                                      r.state->ctx->stream);
+      if (e != cudaSuccess) rc[i] = cuda_fail(e, "vqe_eval_batch");
+    }
+  }
+  mps_status first_bad = MPS_OK;
+  for (size_t i = 0; i < n; ++i) {
+    if (rc[i] == MPS_OK && !on_device) {
+      DeviceGuard guard(reqs[i].state->ctx->device);
+      cudaError_t e = cudaStreamSynchronize(reqs[i].state->ctx->stream);
+      if (e != cudaSuccess) rc[i] = cuda_fail(e, "vqe_eval_batch");
+    }
+    if (rc[i] != MPS_OK) {
+      if (!on_device) energies_out[i] = 0.0;
+      if (first_bad == MPS_OK) first_bad = rc[i];
+    }
+    if (status_out) status_out[i] = rc[i];
+  }
+  return first_bad;
+}
+
+}  // namespace mpsv
+
+extern "C" {
+
+mps_status vqe_eval_batch(const vqe_request* reqs, size_t n, double* energies_out, mps_status* status_out) {
+  return run_batch(reqs, n, energies_out, status_out, false);
+}
+
+mps_status vqe_eval_batch_async(const vqe_request* reqs, size_t n, double* d_energies_out, mps_status* status_out) {
+  return run_batch(reqs, n, d_energies_out, status_out, true);
 }
 
 }  // extern "C"

@@ -99,6 +99,18 @@ struct mps_state {
   size_t total_elems = 0;
   std::vector<uint8_t> last_bits;
   bool broken = false;
+  // circuit binding workspace (per state, so states sharing a circuit can run concurrently)
+  mpsv::DevGate* d_bound = nullptr;
+  size_t bound_cap = 0;
+  double* d_theta = nullptr;
+  size_t theta_cap = 0;
+  // energy workspace (per state, so states sharing a Hamiltonian can run concurrently)
+  void* d_L[2] = {nullptr, nullptr};
+  void* d_M = nullptr;
+  size_t L_bytes = 0, M_bytes = 0;
+  double* d_vals = nullptr;
+  size_t vals_cap = 0;
+  double* d_energy = nullptr;
 };
 
 struct mps_circuit {
@@ -108,8 +120,6 @@ struct mps_circuit {
   int n_gates = 0;
   std::vector<int> q, arity;
   mpsv::DevTmplGate* d_tmpl = nullptr;
-  mpsv::DevGate* d_bound = nullptr;
-  double* d_theta = nullptr;
 };
 
 namespace mpsv {
@@ -131,18 +141,14 @@ struct mps_ham {
   int4* d_leaf = nullptr;
   int2* d_trace = nullptr;
   double* d_coeffs = nullptr;
-  double* d_vals = nullptr;
-  double* d_energy = nullptr;
-  // environment buffers (sized for the largest state seen)
-  void* d_L[2] = {nullptr, nullptr};
-  void* d_M = nullptr;
-  size_t L_bytes = 0, M_bytes = 0;
 };
 
 namespace mpsv {
 // state.cu
 mps_status state_apply_device_gates(mps_state* st, const DevGate* d_gates, const int* q, const int* arity, size_t n);
 mps_status state_reset(mps_state* st, const uint8_t* bits);
+// Copies theta into the state's workspace and binds the circuit's gates there.
+mps_status state_bind_circuit(mps_state* st, const mps_circuit* c, const double* theta, int theta_on_device);
 // energy.cu
 mps_status ham_energy_async(mps_state* st, mps_ham* h, double* d_out);
 }  // namespace mpsv

@@ -136,10 +136,11 @@ template <typename S, typename R> static void svd_set_attr() {
   });
 }
 
-// Cluster size for the Jacobi SVD of a theta with up to mcap columns of
-// A = C~^H and ncap rows, or 0 when the single-CTA kernel is used.
+// Cluster size for the Jacobi SVD of a theta with up to mcap rows and ncap
+// columns (A = C~, stacked columns [A; V] of length mcap + ncap), or 0 when
+// the single-CTA kernel is used.
 template <typename S, typename R> static int cluster_svd_size(int mcap, int ncap) {
-  if (mcap < 96) return 0;
+  if (ncap < 96) return 0;
   static int max16 = -1;
   static std::once_flag f;
   std::call_once(f, [] {
@@ -164,10 +165,10 @@ template <typename S, typename R> static int cluster_svd_size(int mcap, int ncap
     }
     max16 = n;
   });
-  for (int P = (mcap >= 192 && max16 > 0) ? 16 : 8; P <= 16; P *= 2) {
+  for (int P = (ncap >= 192 && max16 > 0) ? 16 : 8; P <= 16; P *= 2) {
     if (P == 16 && max16 <= 0) break;
-    const int b = (mcap + 2 * P - 1) / (2 * P);
-    ClusterSvdSmem<S> L(b, ncap, 2 * P * b, 512);
+    const int b = (ncap + 2 * P - 1) / (2 * P);
+    ClusterSvdSmem<S> L(b, mcap + ncap, 2 * P * b, 512);
     if (L.total + 2048 <= max_dyn_smem()) return P;
   }
   return 0;
@@ -193,8 +194,8 @@ static void launch_two_qubit(mps_state* st, const DevGate* g, int q, cudaStream_
   p.tol = st->cfg.svd_tol;
   const dim3 g3((cap_m + kTile - 1) / kTile, (2 * cap_l + kTile - 1) / kTile);
   if (P) {
-    const int b = (2 * cap_l + 2 * P - 1) / (2 * P);
-    ClusterSvdSmem<S> L(b, 2 * cap_r, 2 * P * b, 512);
+    const int b = (2 * cap_r + 2 * P - 1) / (2 * P);
+    ClusterSvdSmem<S> L(b, 2 * cap_l + 2 * cap_r, 2 * P * b, 512);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(P);
     cfg.blockDim = dim3(512);
@@ -304,13 +305,45 @@ mps_status state_reset(mps_state* st, const uint8_t* bits) {
   return MPS_OK;
 }
 
+mps_status state_bind_circuit(mps_state* st, const mps_circuit* c, const double* theta, int theta_on_device) {
+  mps_ctx* ctx = st->ctx;
+  cudaStream_t s = ctx->stream;
+  if ((size_t)c->n_gates > st->bound_cap) {
+    dev_free(ctx, st->d_bound);
+    st->d_bound = nullptr;
+    st->bound_cap = 0;
+    mps_status rc = dev_alloc(ctx, (void**)&st->d_bound, std::max<size_t>(1, c->n_gates) * sizeof(DevGate));
+    if (rc != MPS_OK) return rc;
+    st->bound_cap = c->n_gates;
+  }
+  if ((size_t)c->n_params > st->theta_cap || !st->d_theta) {
+    dev_free(ctx, st->d_theta);
+    st->d_theta = nullptr;
+    st->theta_cap = 0;
+    mps_status rc = dev_alloc(ctx, (void**)&st->d_theta, std::max(1, c->n_params) * sizeof(double));
+    if (rc != MPS_OK) return rc;
+    st->theta_cap = std::max(1, c->n_params);
+  }
+  if (c->n_params)
+    MPSV_CUDA(cudaMemcpyAsync(st->d_theta, theta, c->n_params * sizeof(double),
+                              theta_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  if (c->n_gates) {
+    KernelScope k(ctx, MPS_K_SETUP);
+    bind_kernel<<<c->n_gates, 32, 0, s>>>(c->d_tmpl, c->n_gates, st->d_theta, st->d_bound);
+  }
+  MPSV_CUDA(cudaGetLastError());
+  return MPS_OK;
+}
+
 static void destroy_state(mps_state* st) {
   if (!st) return;
   mps_ctx* c = st->ctx;
   DeviceGuard guard(c->device);
   cudaStreamSynchronize(c->stream);
   for (void* p : {st->d_B, (void*)st->d_lam, (void*)st->d_chi, (void*)st->d_site_off, (void*)st->d_lam_off,
-                  (void*)st->d_bits, (void*)st->d_rep, st->d_C, st->d_A, st->d_V, (void*)st->d_gates})
+                  (void*)st->d_bits, (void*)st->d_rep, st->d_C, st->d_A, st->d_V, (void*)st->d_gates,
+                  (void*)st->d_bound, (void*)st->d_theta, st->d_L[0], st->d_L[1], st->d_M, (void*)st->d_vals,
+                  (void*)st->d_energy})
     dev_free(c, p);
   delete st;
 }
@@ -710,8 +743,6 @@ mps_status mps_circuit_create(mps_ctx* ctx, int32_t n_qubits, const mps_template
   }
   DeviceGuard guard(ctx->device);
   mps_status rc = dev_alloc(ctx, (void**)&c->d_tmpl, std::max<size_t>(1, n_gates) * sizeof(DevTmplGate));
-  if (rc == MPS_OK) rc = dev_alloc(ctx, (void**)&c->d_bound, std::max<size_t>(1, n_gates) * sizeof(DevGate));
-  if (rc == MPS_OK) rc = dev_alloc(ctx, (void**)&c->d_theta, std::max(1, n_params) * sizeof(double));
   if (rc == MPS_OK && n_gates) {
     cudaError_t e = cudaMemcpyAsync(c->d_tmpl, ht.data(), n_gates * sizeof(DevTmplGate), cudaMemcpyHostToDevice,
                                     ctx->stream);
@@ -720,8 +751,6 @@ mps_status mps_circuit_create(mps_ctx* ctx, int32_t n_qubits, const mps_template
   }
   if (rc != MPS_OK) {
     dev_free(ctx, c->d_tmpl);
-    dev_free(ctx, c->d_bound);
-    dev_free(ctx, c->d_theta);
     delete c;
     return rc;
   }
@@ -734,8 +763,6 @@ void mps_circuit_destroy(mps_circuit* c) {
   DeviceGuard guard(c->ctx->device);
   cudaStreamSynchronize(c->ctx->stream);
   dev_free(c->ctx, c->d_tmpl);
-  dev_free(c->ctx, c->d_bound);
-  dev_free(c->ctx, c->d_theta);
   delete c;
 }
 
@@ -744,8 +771,9 @@ mps_status mps_apply_circuit_async(mps_state* st, const mps_circuit* c, const do
     set_error("mps_apply_circuit_async: NULL argument");
     return MPS_EINVAL;
   }
-  if (c->n != st->n || c->ctx != st->ctx) {
-    set_error("mps_apply_circuit_async: circuit for %d qubits / another context, state has %d", c->n, st->n);
+  if (c->n != st->n || c->ctx->device != st->ctx->device) {
+    set_error("mps_apply_circuit_async: circuit for %d qubits on device %d, state has %d on device %d", c->n,
+              c->ctx->device, st->n, st->ctx->device);
     return MPS_EINVAL;
   }
   if (st->broken) {
@@ -753,24 +781,10 @@ mps_status mps_apply_circuit_async(mps_state* st, const mps_circuit* c, const do
     return MPS_ESTATE;
   }
   DeviceGuard guard(st->ctx->device);
-  cudaStream_t s = st->ctx->stream;
-  const double* d_theta = theta;
-  if (!theta_on_device && c->n_params) {
-    MPSV_CUDA(cudaMemcpyAsync(c->d_theta, theta, c->n_params * sizeof(double), cudaMemcpyHostToDevice, s));
-    d_theta = c->d_theta;
-  }
-  if (c->n_gates) {
-    {
-      KernelScope k(st->ctx, MPS_K_SETUP);
-      bind_kernel<<<c->n_gates, 32, 0, s>>>(c->d_tmpl, c->n_gates, d_theta ? d_theta : c->d_theta, c->d_bound);
-    }
-    mps_status rc = state_apply_device_gates(st, c->d_bound, c->q.data(), c->arity.data(), c->n_gates);
-    if (rc != MPS_OK) {
-      st->broken = true;
-      return rc;
-    }
-  }
-  return MPS_OK;
+  mps_status rc = state_bind_circuit(st, c, theta, theta_on_device);
+  if (rc == MPS_OK && c->n_gates) rc = state_apply_device_gates(st, st->d_bound, c->q.data(), c->arity.data(), c->n_gates);
+  if (rc != MPS_OK) st->broken = true;
+  return rc;
 }
 
 }  // extern "C"

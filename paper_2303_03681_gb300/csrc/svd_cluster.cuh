@@ -1,14 +1,17 @@
 // One-sided Jacobi SVD on a thread-block cluster (Algorithm 1 of the paper's
 // "SVD and one-side jacobi" subsection, parallelised over up to 16 SMs).
 //
-// The kernel orthogonalises the columns of A = C~^H (n_rows = 2 chi_r rows,
-// n_cols = 2 chi_l columns), read from the row-major theta C as
-// A[:, r] = lam_q[r / 2] * conj(C[r, :]).  When the columns are mutually
-// orthogonal, A = W Sigma with W the right singular vectors of C~, so the
-// kept rows of B~_{q+1} = W^H are the conjugated, normalised columns and no
-// rotation accumulator is needed.
+// The kernel orthogonalises the n = 2 chi_r columns of A = C~ (m = 2 chi_l
+// rows, read from the row-major theta C as A[r, c] = lam_q[r / 2] C[r, c])
+// and accumulates the same rotations into V (Algorithm 1: A = A J, V = V J).
+// Each column is stored as the stacked vector [A(:, c); V(:, c)] of length
+// m + n, so one rotation updates both.  When the columns are orthogonal,
+// A = U Sigma and V holds the right singular vectors W; the kept rows of
+// B~_{q+1} = W^H are conjugated columns of V, unitary to rounding for any
+// singular value (normalising columns of A instead would amplify the
+// rounding error of small columns by s_1 / s_j).
 //
-// Parallel order.  The n_cols columns are split into 2P blocks of b columns
+// Parallel order.  The n columns are split into 2P blocks of b columns
 // (zero-padded).  CTA p of the P-CTA cluster holds the blocks at positions p
 // and 2P-1-p of a circle-method round robin over the 2P blocks: in each of
 // the 2P-1 rounds of a sweep every CTA orthogonalises all column pairs
@@ -39,13 +42,13 @@ __device__ __forceinline__ void pos_owner(int pos, int P, int& rank, int& slot) 
 
 template <typename S>
 struct ClusterSvdSmem {
-  // layout of the dynamic shared memory (offsets in bytes)
+  // layout of the dynamic shared memory (offsets in bytes); len = m + n
   size_t buf, red, sig, rank;
   size_t total;
   __host__ __device__ static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-  __host__ __device__ ClusterSvdSmem(int b, int rows, int ncols_pad, int nthreads) {
+  __host__ __device__ ClusterSvdSmem(int b, int len, int ncols_pad, int nthreads) {
     buf = 0;
-    size_t slots = 2ull * 2 * b * rows * sizeof(cplx<S>);  // ping-pong x {top, bottom}
+    size_t slots = 2ull * 2 * b * len * sizeof(cplx<S>);  // ping-pong x {top, bottom}
     red = align16(buf + slots);
     sig = align16(red + 4ull * (nthreads / 32 + 1) * sizeof(S) * 2);
     rank = align16(sig + (size_t)ncols_pad * sizeof(double));
@@ -64,42 +67,49 @@ __global__ void __launch_bounds__(512, 1)
   const int me = (int)cluster.block_rank();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_flag_in[16];
+  __shared__ double s_fro[16];
   __shared__ int s_k;
   __shared__ double s_nrm;
 
   const int chi_l = chi[q], chi_r = chi[q + 2];
-  const int rows = 2 * chi_r;   // length of a column of A = C~^H
-  const int ncols = 2 * chi_l;  // columns to orthogonalise
+  const int m = 2 * chi_l;      // rows of A
+  const int ncols = 2 * chi_r;  // columns of A = rows of V
+  const int len = m + ncols;    // stacked column [A; V]
   const int b = (ncols + 2 * P - 1) / (2 * P);
   const int ncols_pad = 2 * P * b;
   const int nt = blockDim.x;
-  const ClusterSvdSmem<S> L(b, rows, ncols_pad, nt);
+  const ClusterSvdSmem<S> L(b, len, ncols_pad, nt);
   C* bufs = reinterpret_cast<C*>(smem + L.buf);
   S* red = reinterpret_cast<S*>(smem + L.red);
   double* sig = reinterpret_cast<double*>(smem + L.sig);
   int* rnk = reinterpret_cast<int*>(smem + L.rank);
-  const size_t slot_elems = (size_t)b * rows;
-  auto col_ptr = [&](int pp, int slot, int c) -> C* { return bufs + ((size_t)(pp * 2 + slot) * b + c) * rows; };
+  const size_t slot_elems = (size_t)b * len;
+  auto col_ptr = [&](int pp, int slot, int c) -> C* { return bufs + ((size_t)(pp * 2 + slot) * b + c) * len; };
 
   // ---- load: position pos holds the initial block pos (columns pos*b ..)
   for (int slot = 0; slot < 2; ++slot) {
     const int pos = slot == 0 ? me : 2 * P - 1 - me;
     for (size_t t = threadIdx.x; t < slot_elems; t += nt) {
-      const int c = (int)(t / rows), r = (int)(t % rows);
+      const int c = (int)(t / len), r = (int)(t % len);
       const int col = pos * b + c;
       C v = cmk<S>(0, 0);
       if (col < ncols) {
-        const cplx<R> x = Cm[(size_t)col * rows + r];
-        const S w = S(lam_l[col >> 1]);
-        v = cmk<S>(w * S(x.x), -w * S(x.y));
+        if (r < m) {
+          const cplx<R> x = Cm[(size_t)r * ncols + col];
+          const S w = S(lam_l[r >> 1]);
+          v = cmk<S>(w * S(x.x), w * S(x.y));
+        } else if (r - m == col) {
+          v = cmk<S>(1, 0);
+        }
       }
       col_ptr(0, slot, c)[r] = v;
     }
   }
+  __syncthreads();
   // ||A||_F^2: each CTA's share goes to every CTA, summed in rank order
-  __shared__ double s_fro[16];
   double part = 0.0;
   for (size_t t = threadIdx.x; t < 2 * slot_elems; t += nt) {
+    if ((int)(t % len) >= m) continue;
     const C v = bufs[t];
     part += double(v.x) * v.x + double(v.y) * v.y;
   }
@@ -114,13 +124,11 @@ __global__ void __launch_bounds__(512, 1)
   for (int r2 = 0; r2 < P; ++r2) fro2 += s_fro[r2];
 
   // Stopping rule and rounding floor: rotate while |b_ij| > tol sqrt(b_ii b_jj)
-  // with tol = 4 sqrt(max(rows, cols)) u (a few times the rounding error of a
-  // dot product); columns with squared norm below (4 u ||A||_F)^2 are rounding
-  // noise and left alone.  The floor must stay far below any kept singular
-  // value: without a rotation accumulator an unrotated column would become a
-  // non-orthogonal row of B~_{q+1}.
+  // with tol = 4 sqrt(max(m, n)) u (a few times the rounding error of a dot
+  // product); columns with squared norm below (4 u ||A||_F)^2 are rounding
+  // noise and left alone.
   const S eps_u = sizeof(S) == 8 ? S(1.1102230246251565e-16) : S(5.9604645e-08f);
-  const S tol = p.tol > 0 ? S(p.tol) : S(4.0 * sqrt(double(max(rows, ncols)))) * eps_u;
+  const S tol = p.tol > 0 ? S(p.tol) : S(4.0 * sqrt(double(max(m, ncols)))) * eps_u;
   const S floor = S(16.0 * double(eps_u) * double(eps_u) * fro2);
   const S tiny = sizeof(S) == 8 ? S(1e-290) : S(1e-35f);
   // threads per pair: the largest power of two with b groups in the block
@@ -158,7 +166,7 @@ __global__ void __launch_bounds__(512, 1)
         C* ai = col_ptr(cur, si, active ? ci : 0);
         C* aj = col_ptr(cur, sj, active ? cj : 0);
         S alpha = 0, beta = 0, gr = 0, gi = 0;
-        for (int r = lt; active && r < rows; r += T) {
+        for (int r = lt; active && r < m; r += T) {
           const C x = ai[r], y = aj[r];
           alpha = fma(x.x, x.x, fma(x.y, x.y, alpha));
           beta = fma(y.x, y.x, fma(y.y, y.y, beta));
@@ -204,7 +212,7 @@ __global__ void __launch_bounds__(512, 1)
           const S c = S(1) / sqrt(S(1) + t * t);
           const S s = t * c;
           const C sph = cmk<S>(s * phr, s * phi);
-          for (int r = lt; r < rows; r += T) {
+          for (int r = lt; r < len; r += T) {  // the A and V parts of both columns
             const C x = ai[r], y = aj[r];
             C ni = cmk<S>(c * x.x, c * x.y);
             ni = csub(ni, cmulc(sph, y));
@@ -251,12 +259,12 @@ __global__ void __launch_bounds__(512, 1)
     }
   }
 
-  // ---- singular values: column norms, shared with every CTA
+  // ---- singular values: norms of the A parts, shared with every CTA
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nt >> 5;
   for (int c = warp; c < 2 * b; c += nw) {
     const C* a = col_ptr(cur, c / b, c % b);
     double acc = 0.0;
-    for (int r = lane; r < rows; r += 32) acc += double(a[r].x) * a[r].x + double(a[r].y) * a[r].y;
+    for (int r = lane; r < m; r += 32) acc += double(a[r].x) * a[r].x + double(a[r].y) * a[r].y;
     acc = warp_sum(acc);
     if (lane == 0) {
       const double sv = sqrt(acc);
@@ -277,8 +285,6 @@ __global__ void __launch_bounds__(512, 1)
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    // the sorted values, by scattering through the ranks into red-free scratch:
-    // walk ranks in order using a local search (ncols_pad is small)
     double total = 0.0, smax = 0.0;
     for (int g = 0; g < ncols_pad; ++g) {
       total += sig[g] * sig[g];
@@ -287,7 +293,7 @@ __global__ void __launch_bounds__(512, 1)
     int cnt = 0;
     for (int g = 0; g < ncols_pad; ++g)
       if (p.trunc_rel > 0.0 ? (sig[g] > p.trunc_rel * smax) : (sig[g] > 0.0)) ++cnt;
-    int k = min(cnt, min(p.chi_max, min(rows, ncols)));
+    int k = min(cnt, min(p.chi_max, min(m, ncols)));
     if (k < 1) k = 1;
     double kept = 0.0, smin = 0.0, s_next = 0.0;
     for (int g = 0; g < ncols_pad; ++g) {
@@ -309,9 +315,9 @@ __global__ void __launch_bounds__(512, 1)
       const int used = converged ? sweep : p.max_sweeps + 1;
       if (used > rep->max_sweeps) rep->max_sweeps = used;
       rep->two_qubit_gates += 1;
-      // per sweep and column pair: three dot products (16 rows flops) and one
-      // rotation of the two columns (12 rows flops)
-      rep->svd_flops += (double)min(used, p.max_sweeps) * 0.5 * ncols * (ncols - 1) * 28.0 * rows;
+      // per sweep and column pair: three dot products over m rows (16 m flops)
+      // and one rotation of the stacked columns (12 (m + n) flops)
+      rep->svd_flops += (double)min(used, p.max_sweeps) * 0.5 * ncols * (ncols - 1) * (16.0 * m + 12.0 * len);
       rep->inv_norm = 1.0 / nrm;
       chi[q + 1] = k;
     }
@@ -322,18 +328,13 @@ __global__ void __launch_bounds__(512, 1)
   if (me == 0)
     for (int g = threadIdx.x; g < ncols_pad; g += nt)
       if (rnk[g] < k) lam_next[rnk[g]] = sig[g] * inv;
-  // B~_{q+1}[a, :] = conj(A[:, g]) / sigma_g for the column g of rank a < k
+  // B~_{q+1}[a, :] = conj(V[:, g]) for the column g of rank a < k
   for (int c = warp; c < 2 * b; c += nw) {
     const int g = me * 2 * b + c;
     const int a = rnk[g];
     if (a >= k) continue;
-    const double sv = sig[g];
-    const S is = sv > 0.0 ? S(1.0 / sv) : S(0);
-    const C* col = col_ptr(cur, c / b, c % b);
-    for (int r = lane; r < rows; r += 32) {
-      const C v = col[r];
-      Bnext[(size_t)a * rows + r] = ccast<cplx<R>>(cmk<S>(v.x * is, -v.y * is));
-    }
+    const C* v = col_ptr(cur, c / b, c % b) + m;
+    for (int r = lane; r < ncols; r += 32) Bnext[(size_t)a * ncols + r] = ccast<cplx<R>>(cconj(v[r]));
   }
   cluster.sync();  // no CTA leaves while its shared memory may still be read
 }

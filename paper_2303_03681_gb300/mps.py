@@ -87,6 +87,8 @@ def _load():
         "mps_export": ([P, P, SZ, P, SZ], ctypes.c_int),
         "mps_get_report": ([P, ctypes.POINTER(Report)], ctypes.c_int),
         "vqe_eval": ([P, P, SZ, P, P], ctypes.c_int),
+        "vqe_eval_batch": ([P, SZ, P, P], ctypes.c_int),
+        "vqe_eval_batch_async": ([P, SZ, P, P], ctypes.c_int),
         "mps_ctx_profile": ([P, ctypes.c_uint32], ctypes.c_int),
         "mps_ctx_profile_read": ([P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                   ctypes.POINTER(D), I32], ctypes.c_int),
@@ -392,4 +394,52 @@ def vqe_eval(ctx: Context, requests):
     rc = _lib.vqe_eval(ctx.handle, reqs, n, _ptr(energies), _ptr(status))
     if rc != MPS_OK and np.all(status == MPS_OK):
         _check(rc)
+    return energies, status
+
+
+def _requests(requests):
+    n = len(requests)
+    reqs = (VqeRequest * n)()
+    keep = []
+    for i, (st, circ, ham, theta, bits) in enumerate(requests):
+        if isinstance(theta, int):  # a device pointer
+            th_ptr = theta
+        else:
+            th = np.ascontiguousarray(theta, dtype=np.float64)
+            keep.append(th)
+            th_ptr = th.ctypes.data
+        b = None if bits is None else np.ascontiguousarray(bits, dtype=np.uint8)
+        keep.append(b)
+        reqs[i] = VqeRequest(st.handle.value, circ.handle.value, ham.handle.value, th_ptr,
+                             None if b is None else b.ctypes.data)
+    return reqs, keep
+
+
+def vqe_eval_batch_async(requests, d_energies_ptr: int):
+    """Device-resident batch: every theta is a device pointer (int) and the
+    energies go to the device array at d_energies_ptr.  Returns the statuses;
+    the work is still running on the states' streams."""
+    reqs, keep = _requests(requests)
+    n = len(requests)
+    status = np.zeros(n, dtype=np.int32)
+    rc = _lib.vqe_eval_batch_async(reqs, n, ctypes.c_void_p(int(d_energies_ptr)), _ptr(status))
+    if rc != MPS_OK:
+        _check(rc)
+    del keep
+    return status
+
+
+def vqe_eval_batch(requests):
+    """Independent evaluations overlapped on the device.  requests: list of
+    (State, Circuit, Hamiltonian, theta, init_bits or None) with distinct
+    states (each state's context stream carries its work).
+    Returns (energies, statuses)."""
+    reqs, keep = _requests(requests)
+    n = len(requests)
+    energies = np.zeros(n)
+    status = np.zeros(n, dtype=np.int32)
+    rc = _lib.vqe_eval_batch(reqs, n, _ptr(energies), _ptr(status))
+    if rc != MPS_OK and np.all(status == MPS_OK):
+        _check(rc)
+    del keep
     return energies, status

@@ -119,14 +119,19 @@ def test_svd_global_memory_path(mps, ctx):
     assert om.fidelity(got, ref) >= 1 - 1e-10
 
 
-@pytest.mark.parametrize("precision,svd64,chi", [("fp32", False, 48), ("fp32", False, 100), ("fp32", True, 64),
-                                                 ("fp64", True, 128)])
-def test_cluster_svd_path(mps, ctx, precision, svd64, chi):
-    """Thetas with 2 chi_l >= 96 columns take the thread-block-cluster Jacobi
-    (8 CTAs below 192 columns, 16 above); ragged chi pads the column blocks."""
-    n = 16
-    circ = brickwork_circuit(n, 14, make_rng(MASTER_SEED + 12))
-    trunc = 1e-6 if precision == "fp32" else 1e-12
+@pytest.mark.parametrize("n,layers,precision,svd64,chi", [(14, 10, "fp32", False, 128), (14, 10, "fp32", False, 60),
+                                                          (13, 9, "fp32", True, 64), (16, 14, "fp64", True, 100)])
+def test_cluster_svd_path(mps, ctx, n, layers, precision, svd64, chi):
+    """Thetas with 2 chi_r >= 96 columns take the thread-block-cluster Jacobi
+    (8 CTAs below 192 columns, 16 above); ragged chi pads the column blocks.
+
+    Complex64 runs compare where truncation does not decide the outcome
+    (chi_max at the exact rank, or a chi = 60 cap on a shallow circuit whose
+    spectrum has a gap there): heavily truncated random circuits amplify any
+    rounding difference, so an FP32 run and the FP64 oracle follow different
+    truncated states there."""
+    circ = brickwork_circuit(n, layers, make_rng(MASTER_SEED + 12))
+    trunc = 1e-5 if precision == "fp32" else 1e-12
     ref = om.run_circuit(n, None, circ, chi_max=chi, eps_rel=trunc)
     st = mps.State(ctx, n, None, chi_max=chi, precision=precision, trunc_rel=trunc, svd_fp64=svd64)
     rep = st.apply_gates(circ)
@@ -134,14 +139,18 @@ def test_cluster_svd_path(mps, ctx, precision, svd64, chi):
     got = to_oracle(st)
     ham = random_local_pauli_sum(n, 300, make_rng(MASTER_SEED + 13))
     e = st.energy(mps.Hamiltonian(ctx, ham))
+    dw = max(rep["discarded_weight"], ref.stats.discarded_weight)
+    print(f"\ncluster n={n} chi={chi} {precision} svd64={svd64}: dE={e - om.energy(ref, ham):.3e} "
+          f"1-F={1 - om.fidelity(got, ref):.3e} dw={dw:.3e} chi={max(st.bond_dims())}/{max(ref.bond_dims())}")
     if precision == "fp64":
         assert list(st.bond_dims()) == ref.bond_dims()
         assert spectra_close(got.lam, ref.lam, 1e-9)
         assert abs(e - om.energy(ref, ham)) <= 1e-9
         assert om.fidelity(got, ref) >= 1 - 1e-10
     else:
-        assert abs(e - om.energy(ref, ham)) <= 2e-5
-        assert om.fidelity(got, ref) >= 1 - 1e-5
+        assert 1 - om.fidelity(got, ref) <= 1e-6 + 4 * dw
+        assert abs(e - om.energy(ref, ham)) <= 1e-5 + 40 * np.sqrt(dw)
+        assert om.canonical_residual(got) <= 1e-4
 
 
 def test_uccsd_template_through_vqe_eval(mps, ctx):
@@ -244,3 +253,27 @@ def test_allocation_cap_gives_enomem(mps):
     c.set_alloc_limit(0)
     st = mps.State(c, 6, None, chi_max=4)
     assert st.bond_dims().sum() == 7
+
+
+def test_batch_results_equal_single_results(mps):
+    """Each evaluation gives the same energy alone (vqe_eval) and in a batch of
+    concurrent evaluations on separate streams (vqe_eval_batch)."""
+    n_so, n_e = 8, 4
+    rng = make_rng(MASTER_SEED + 31)
+    h, g = random_integrals(n_so // 2, rng)
+    ham = jw_molecular_hamiltonian(h, g)
+    tmpl = uccsd_template(n_so, n_e)
+    bits = hf_bits(n_so, n_e)
+    thetas = [rng.uniform(-0.3, 0.3, tmpl.n_params) for _ in range(4)]
+    ctxs = [mps.Context(0) for _ in thetas]
+    circ = mps.Circuit(ctxs[0], tmpl)
+    H = mps.Hamiltonian(ctxs[0], ham)
+    states = [mps.State(c, n_so, bits, chi_max=16, precision="fp64") for c in ctxs]
+    batch, status = mps.vqe_eval_batch([(s, circ, H, th, bits) for s, th in zip(states, thetas)])
+    assert list(status) == [0] * len(thetas)
+    for s, c, th, e in zip(states, ctxs, thetas, batch):
+        alone, st2 = mps.vqe_eval(c, [(s, circ, H, th, bits)])
+        assert st2[0] == 0 and alone[0] == e
+        assert abs(e - om.vqe_energy(tmpl, th, bits, ham, chi_max=16)) <= 1e-10
+    with pytest.raises(mps.MpsError):
+        mps.vqe_eval_batch([(states[0], circ, H, thetas[0], bits), (states[0], circ, H, thetas[1], bits)])
