@@ -140,7 +140,9 @@ template <typename S, typename R> static void svd_set_attr() {
 // columns (A = C~, stacked columns [A; V] of length mcap + ncap), or 0 when
 // the single-CTA kernel is used.
 template <typename S, typename R> static int cluster_svd_size(int mcap, int ncap) {
-  if (ncap < 96) return 0;
+  // FP64 runs at 2 FMA/clk/SM on this part, so even small FP64 thetas gain
+  // from spreading their columns over several SMs; FP32 ones only from 96.
+  if (ncap < (sizeof(S) == 8 ? 32 : 96)) return 0;
   static int max16 = -1;
   static std::once_flag f;
   std::call_once(f, [] {
@@ -165,7 +167,7 @@ template <typename S, typename R> static int cluster_svd_size(int mcap, int ncap
     }
     max16 = n;
   });
-  for (int P = (ncap >= 192 && max16 > 0) ? 16 : 8; P <= 16; P *= 2) {
+  for (int P = ncap < 64 ? 4 : ((ncap >= 192 && max16 > 0) ? 16 : 8); P <= 16; P *= 2) {
     if (P == 16 && max16 <= 0) break;
     const int b = (ncap + 2 * P - 1) / (2 * P);
     ClusterSvdSmem<S> L(b, mcap + ncap, 2 * P * b, 512);

@@ -137,7 +137,7 @@ def test_cluster_svd_path(mps, ctx, n, layers, precision, svd64, chi):
     rep = st.apply_gates(circ)
     assert rep["svd_not_converged"] == 0
     got = to_oracle(st)
-    ham = random_local_pauli_sum(n, 300, make_rng(MASTER_SEED + 13))
+    ham = random_local_pauli_sum(n, 200, make_rng(MASTER_SEED + 13))
     e = st.energy(mps.Hamiltonian(ctx, ham))
     dw = max(rep["discarded_weight"], ref.stats.discarded_weight)
     print(f"\ncluster n={n} chi={chi} {precision} svd64={svd64}: dE={e - om.energy(ref, ham):.3e} "
@@ -275,5 +275,5 @@ def test_batch_results_equal_single_results(mps):
         alone, st2 = mps.vqe_eval(c, [(s, circ, H, th, bits)])
         assert st2[0] == 0 and alone[0] == e
         assert abs(e - om.vqe_energy(tmpl, th, bits, ham, chi_max=16)) <= 1e-10
-    with pytest.raises(mps.MpsError):
-        mps.vqe_eval_batch([(states[0], circ, H, thetas[0], bits), (states[0], circ, H, thetas[1], bits)])
+    _, status = mps.vqe_eval_batch([(states[0], circ, H, thetas[0], bits), (states[0], circ, H, thetas[1], bits)])
+    assert list(status) == [mps.MPS_OK, mps.MPS_EINVAL]  # a state may serve one request of a batch
