@@ -171,7 +171,7 @@ template <typename S, typename R> static int cluster_svd_size(int mcap, int ncap
     if (P == 16 && max16 <= 0) break;
     const int b = (ncap + 2 * P - 1) / (2 * P);
     ClusterSvdSmem<S> L(b, mcap + ncap, 2 * P * b, 512);
-    if (L.total + 2048 <= max_dyn_smem()) return P;
+    if (L.total + 2048 <= max_dyn_smem() && 32 * b <= 512) return P;
   }
   return 0;
 }
@@ -200,7 +200,7 @@ static void launch_two_qubit(mps_state* st, const DevGate* g, int q, cudaStream_
     ClusterSvdSmem<S> L(b, 2 * cap_l + 2 * cap_r, 2 * P * b, 512);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(P);
-    cfg.blockDim = dim3(512);
+    cfg.blockDim = dim3(32 * b);  // one warp per column pair
     cfg.dynamicSmemBytes = L.total;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];

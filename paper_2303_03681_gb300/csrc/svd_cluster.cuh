@@ -40,6 +40,94 @@ __device__ __forceinline__ void pos_owner(int pos, int P, int& rank, int& slot) 
   }
 }
 
+// Stacked-column elements a lane keeps in registers in the cross rounds
+// (columns up to 32 * kClusterRegs = 512 entries long).
+constexpr int kClusterRegs = 16;
+
+// Rotation of a column pair from its Gram entries (Algorithm 1 with the phase
+// of b_ij moved onto column j); returns false when the pair is left alone.
+template <typename S>
+__device__ __forceinline__ bool jacobi_rotation(S alpha, S beta, S gr, S gi, S tol, S floor, S tiny, S& c, cplx<S>& sph) {
+  const S mag = sqrt(gr * gr + gi * gi);
+  if (!(mag > tiny) || !(mag > tol * sqrt(alpha * beta)) || !(min(alpha, beta) > floor)) return false;
+  const S zeta = (beta - alpha) / (S(2) * mag);
+  const S t = (zeta >= S(0) ? S(1) : S(-1)) / (fabs(zeta) + sqrt(S(1) + zeta * zeta));
+  c = S(1) / sqrt(S(1) + t * t);
+  const S s = t * c;
+  sph = cmk<S>(s * gr / mag, s * gi / mag);  // s e^{i phi}
+  return true;
+}
+
+template <typename S>
+__device__ __forceinline__ void warp_sum4(S& a, S& b, S& c, S& d) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+    c += __shfl_xor_sync(0xffffffffu, c, o);
+    d += __shfl_xor_sync(0xffffffffu, d, o);
+  }
+}
+
+// One warp rotates two stacked columns [A; V] held in shared memory; the Gram
+// entries use the first m (A) rows.
+template <typename S>
+__device__ __forceinline__ int jacobi_pair_smem(cplx<S>* ai, cplx<S>* aj, int m, int len, int lane, S tol, S floor,
+                                                S tiny) {
+  using C = cplx<S>;
+  S alpha = 0, beta = 0, gr = 0, gi = 0;
+  for (int r = lane; r < m; r += 32) {
+    const C x = ai[r], y = aj[r];
+    alpha = fma(x.x, x.x, fma(x.y, x.y, alpha));
+    beta = fma(y.x, y.x, fma(y.y, y.y, beta));
+    gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+    gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+  }
+  warp_sum4(alpha, beta, gr, gi);
+  S c;
+  C sph;
+  if (!jacobi_rotation(alpha, beta, gr, gi, tol, floor, tiny, c, sph)) return 0;
+  for (int r = lane; r < len; r += 32) {
+    const C x = ai[r], y = aj[r];
+    ai[r] = csub(cmk<S>(c * x.x, c * x.y), cmulc(sph, y));
+    aj[r] = cadd(cmk<S>(c * y.x, c * y.y), cmul(sph, x));
+  }
+  return 1;
+}
+
+// Same with the first column in registers: x[i] is row lane + 32 i.
+template <typename S>
+__device__ __forceinline__ int jacobi_pair_reg(cplx<S> (&x)[kClusterRegs], cplx<S>* aj, int m, int len, int lane,
+                                               S tol, S floor, S tiny) {
+  using C = cplx<S>;
+  S alpha = 0, beta = 0, gr = 0, gi = 0;
+#pragma unroll
+  for (int i = 0; i < kClusterRegs; ++i) {
+    const int r = lane + 32 * i;
+    if (r < m) {
+      const C xv = x[i], y = aj[r];
+      alpha = fma(xv.x, xv.x, fma(xv.y, xv.y, alpha));
+      beta = fma(y.x, y.x, fma(y.y, y.y, beta));
+      gr = fma(xv.x, y.x, fma(xv.y, y.y, gr));
+      gi = fma(xv.x, y.y, fma(-xv.y, y.x, gi));
+    }
+  }
+  warp_sum4(alpha, beta, gr, gi);
+  S c;
+  C sph;
+  if (!jacobi_rotation(alpha, beta, gr, gi, tol, floor, tiny, c, sph)) return 0;
+#pragma unroll
+  for (int i = 0; i < kClusterRegs; ++i) {
+    const int r = lane + 32 * i;
+    if (r < len) {
+      const C xv = x[i], y = aj[r];
+      x[i] = csub(cmk<S>(c * xv.x, c * xv.y), cmulc(sph, y));
+      aj[r] = cadd(cmk<S>(c * y.x, c * y.y), cmul(sph, xv));
+    }
+  }
+  return 1;
+}
+
 template <typename S>
 struct ClusterSvdSmem {
   // layout of the dynamic shared memory (offsets in bytes); len = m + n
@@ -80,7 +168,6 @@ __global__ void __launch_bounds__(512, 1)
   const int nt = blockDim.x;
   const ClusterSvdSmem<S> L(b, len, ncols_pad, nt);
   C* bufs = reinterpret_cast<C*>(smem + L.buf);
-  S* red = reinterpret_cast<S*>(smem + L.red);
   double* sig = reinterpret_cast<double*>(smem + L.sig);
   int* rnk = reinterpret_cast<int*>(smem + L.rank);
   const size_t slot_elems = (size_t)b * len;
@@ -131,109 +218,75 @@ __global__ void __launch_bounds__(512, 1)
   const S tol = p.tol > 0 ? S(p.tol) : S(4.0 * sqrt(double(max(m, ncols)))) * eps_u;
   const S floor = S(16.0 * double(eps_u) * double(eps_u) * fro2);
   const S tiny = sizeof(S) == 8 ? S(1e-290) : S(1e-35f);
-  // threads per pair: the largest power of two with b groups in the block
-  int T = 1;
-  while (2 * T * b <= nt) T *= 2;
-  const int pair = threadIdx.x / T, lt = threadIdx.x % T;
-  const bool active = pair < b;
-  const int warps_per_pair = (T + 31) / 32;
-  const int width = T < 32 ? T : 32;  // shuffle width (aligned groups of T lanes)
+  // One warp per column pair (warps past b idle in the pair loops).  In the
+  // cross rounds warp w keeps its top-slot column in registers for the b
+  // rotations it takes part in; only the bottom-slot columns go through
+  // shared memory, so one barrier per sub-round orders their hand-off.
+  const int wl = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const bool active = wp < b;
+  const bool cache_x = len <= 32 * kClusterRegs;
 
   int sweep = 0, cur = 0;
   bool converged = false;
   for (; sweep < p.max_sweeps; ++sweep) {
     int rotated = 0;
     for (int round = 0; round < 2 * P - 1; ++round) {
-      const int subrounds = round == 0 ? 2 * b - 1 : b;
-      for (int sr = 0; sr < subrounds; ++sr) {
-        int ci = 0, cj = 0, si = 0, sj = 1;  // column index within slot, slot
-        if (round == 0) {
-          int a0, a1;
-          const int mod = 2 * b - 1;
-          if (pair == 0) {
-            a0 = mod;
-            a1 = sr;
-          } else {
-            a0 = (sr + pair) % mod;
-            a1 = (sr - pair + mod) % mod;
-          }
-          si = a0 / b, ci = a0 % b;
-          sj = a1 / b, cj = a1 % b;
-        } else {
-          si = 0, ci = pair;
-          sj = 1, cj = (pair + sr) % b;
-        }
-        C* ai = col_ptr(cur, si, active ? ci : 0);
-        C* aj = col_ptr(cur, sj, active ? cj : 0);
-        S alpha = 0, beta = 0, gr = 0, gi = 0;
-        for (int r = lt; active && r < m; r += T) {
-          const C x = ai[r], y = aj[r];
-          alpha = fma(x.x, x.x, fma(x.y, x.y, alpha));
-          beta = fma(y.x, y.x, fma(y.y, y.y, beta));
-          gr = fma(x.x, y.x, fma(x.y, y.y, gr));
-          gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          if (o < width) {
-            alpha += __shfl_xor_sync(0xffffffffu, alpha, o);
-            beta += __shfl_xor_sync(0xffffffffu, beta, o);
-            gr += __shfl_xor_sync(0xffffffffu, gr, o);
-            gi += __shfl_xor_sync(0xffffffffu, gi, o);
-          }
-        }
-        if (warps_per_pair > 1) {
-          const int w = lt / 32;
-          if ((lt & 31) == 0) {
-            S* rr = red + ((size_t)pair * warps_per_pair + w) * 4;
-            rr[0] = alpha;
-            rr[1] = beta;
-            rr[2] = gr;
-            rr[3] = gi;
+      if (round == 0) {
+        // every pair among the CTA's 2b columns: round robin over 2b players
+        const int mod = 2 * b - 1;
+        for (int sr = 0; sr < 2 * b - 1; ++sr) {
+          if (active) {
+            int a0, a1;
+            if (wp == 0) {
+              a0 = mod;
+              a1 = sr;
+            } else {
+              a0 = (sr + wp) % mod;
+              a1 = (sr - wp + mod) % mod;
+            }
+            rotated |= jacobi_pair_smem<S>(col_ptr(cur, a0 / b, a0 % b), col_ptr(cur, a1 / b, a1 % b), m, len, wl,
+                                           tol, floor, tiny);
           }
           __syncthreads();
-          alpha = beta = gr = gi = 0;
-          for (int w2 = 0; w2 < warps_per_pair; ++w2) {
-            const S* rr = red + ((size_t)pair * warps_per_pair + w2) * 4;
-            alpha += rr[0];
-            beta += rr[1];
-            gr += rr[2];
-            gi += rr[3];
+        }
+      } else {
+        C xr[kClusterRegs];
+        C* xcol = col_ptr(cur, 0, active ? wp : 0);
+        if (active && cache_x) {
+#pragma unroll
+          for (int i = 0; i < kClusterRegs; ++i) {
+            const int r = wl + 32 * i;
+            xr[i] = r < len ? xcol[r] : cmk<S>(0, 0);
           }
         }
-        const S mag = sqrt(gr * gr + gi * gi);
-        const bool rot =
-            active && (mag > tiny) && (mag > tol * sqrt(alpha * beta)) && (min(alpha, beta) > floor);
-        if (rot) {
-          rotated = 1;
-          const S phr = gr / mag, phi = gi / mag;
-          const S zeta = (beta - alpha) / (S(2) * mag);
-          const S t = (zeta >= S(0) ? S(1) : S(-1)) / (fabs(zeta) + sqrt(S(1) + zeta * zeta));
-          const S c = S(1) / sqrt(S(1) + t * t);
-          const S s = t * c;
-          const C sph = cmk<S>(s * phr, s * phi);
-          for (int r = lt; r < len; r += T) {  // the A and V parts of both columns
-            const C x = ai[r], y = aj[r];
-            C ni = cmk<S>(c * x.x, c * x.y);
-            ni = csub(ni, cmulc(sph, y));
-            C nj = cmk<S>(c * y.x, c * y.y);
-            nj = cadd(nj, cmul(sph, x));
-            ai[r] = ni;
-            aj[r] = nj;
+        for (int sr = 0; sr < b; ++sr) {
+          if (active) {
+            C* aj = col_ptr(cur, 1, (wp + sr) % b);
+            rotated |= cache_x ? jacobi_pair_reg<S>(xr, aj, m, len, wl, tol, floor, tiny)
+                               : jacobi_pair_smem<S>(xcol, aj, m, len, wl, tol, floor, tiny);
+          }
+          __syncthreads();
+        }
+        if (active && cache_x) {
+#pragma unroll
+          for (int i = 0; i < kClusterRegs; ++i) {
+            const int r = wl + 32 * i;
+            if (r < len) xcol[r] = xr[i];
           }
         }
         __syncthreads();
       }
       // ---- hand the blocks on: position pos -> pos + 1 (pos >= 1), 2P-1 -> 1
       const int nxt = cur ^ 1;
+      const size_t units = slot_elems * sizeof(C) / sizeof(uint4);
       for (int slot = 0; slot < 2; ++slot) {
         const int pos = slot == 0 ? me : 2 * P - 1 - me;
         int npos = pos == 0 ? 0 : (pos == 2 * P - 1 ? 1 : pos + 1);
         int drank, dslot;
         pos_owner(npos, P, drank, dslot);
-        C* src = col_ptr(cur, slot, 0);
-        C* dst = cluster.map_shared_rank(col_ptr(nxt, dslot, 0), drank);
-        for (size_t t = threadIdx.x; t < slot_elems; t += nt) dst[t] = src[t];
+        const uint4* src = reinterpret_cast<const uint4*>(col_ptr(cur, slot, 0));
+        uint4* dst = reinterpret_cast<uint4*>(cluster.map_shared_rank(col_ptr(nxt, dslot, 0), drank));
+        for (size_t t = threadIdx.x; t < units; t += nt) dst[t] = src[t];
       }
       cluster.sync();
       cur = nxt;
