@@ -396,6 +396,8 @@ def run_gpu(args):
         "hbm_bytes_allocated": hbm_bytes,
         "wall_s_timed_region": wall,
     }
+    if args.serve_requests > 0:
+        line["serving"] = serve_phase(mps, local, C, H, w, args, rate=0.9 * value / world)
     if world == 1 and not args.no_cpu_baseline:
         step_s, sample = oracle_sample(w)
         line["cpu_baseline"] = {"value": 1.0 / step_s, "unit": "evals/s", "cores": blas_threads(), "kind": "oracle",
@@ -403,6 +405,36 @@ def run_gpu(args):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def serve_phase(mps, device, C, H, w, args, rate):
+    """Poisson-arriving requests (mean rate `rate`/s, about 90 % of the batched
+    throughput) against a continuous-batching server with --batch slots."""
+    srv = mps.Server(device, max_slots=args.batch)
+    frag = srv.add_fragment(C, H, w["bits"], chi_max=w["chi"], precision=w["precision"], trunc_rel=w["trunc"],
+                            svd_fp64=(args.svd == "fp64"))
+    rng = make_rng(MASTER_SEED + 77)
+    gaps = rng.exponential(1.0 / max(rate, 1e-6), args.serve_requests)
+    thetas = thetas_for(w, args.serve_requests, MASTER_SEED + 78)
+    t0 = time.perf_counter()
+    tickets = []
+    for k in range(args.serve_requests):
+        target = t0 + float(np.sum(gaps[:k + 1]))
+        delay = target - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit(frag, thetas[k]))
+    lat = []
+    for t in tickets:
+        e, l_ms = srv.poll(t, timeout_ms=-1)
+        lat.append(l_ms)
+    elapsed = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    return {"requests": args.serve_requests, "arrival_rate_per_s": rate, "slots": args.batch,
+            "throughput_evals_per_s": args.serve_requests / elapsed,
+            "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99)),
+            "hbm_peak_bytes": st["peak_bytes"]}
 
 
 def merge_profiles(profs):
@@ -428,6 +460,8 @@ def main():
                     help="Jacobi SVD precision (default: fp64 for complex128 states, fp32 for complex64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=1, help="concurrent evaluations per step")
+    ap.add_argument("--serve-requests", type=int, default=0,
+                    help="after the timed steps, serve this many Poisson-arriving requests (p50/p99 latency)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -228,6 +228,43 @@ mps_status vqe_eval_batch(const vqe_request* reqs, size_t n, double* energies_ou
  * waits for that state's circuit); synchronise the streams before reading. */
 mps_status vqe_eval_batch_async(const vqe_request* reqs, size_t n, double* d_energies_out, mps_status* status_out);
 
+/* ---- serving: continuous batching of energy evaluations -----------------
+ *
+ * A server owns up to max_slots evaluation slots on one device, each with its
+ * own stream and state.  Fragments (circuit template + Hamiltonian + reference
+ * state + mps_config) are registered once and stay resident.  vqe_submit
+ * queues E(theta) for a fragment and returns at once; a native worker thread
+ * admits queued requests into free slots while the device memory the server
+ * has allocated plus the request's estimated footprint stays within
+ * hbm_budget_bytes (0 = no budget), issues every admitted evaluation's gates
+ * a few at a time in turn (requests arriving while others run join between
+ * gate groups), evaluates its energy and completes it.  This is the paper's
+ * fragment-level parallelism (L298) mapped to one GPU.  The result of a
+ * request does not depend on what else is in flight: the same kernels run on
+ * the same data.  Handles passed to a server (circuit, Hamiltonian) must
+ * outlive it. */
+typedef struct mps_server mps_server;
+
+mps_status mps_server_create(int device, int32_t max_slots, size_t hbm_budget_bytes, mps_server** out);
+/* Register a resident fragment; init_bits: n bytes (NULL = |0...0>). */
+mps_status mps_server_add_fragment(mps_server* srv, const mps_circuit* circuit, const mps_ham* ham,
+                                   const uint8_t* init_bits, const mps_config* cfg, int32_t* fragment_out);
+/* Queue E(theta) for a fragment (theta: host, copied); MPS_EBUSY when the
+ * queue holds max_queue requests already. */
+mps_status vqe_submit(mps_server* srv, int32_t fragment, const double* theta, uint64_t* ticket_out);
+/* Wait up to timeout_ms (0 = do not wait, < 0 = forever) for a request.
+ * Returns MPS_OK with the energy and the submit-to-completion latency in
+ * milliseconds, MPS_ETIMEOUT if it is not done yet, MPS_EINVAL for an unknown
+ * ticket, or the request's own failure status.  A completed ticket is
+ * released by the poll that returns it. */
+mps_status vqe_poll(mps_server* srv, uint64_t ticket, int32_t timeout_ms, double* energy_out, double* latency_ms_out);
+/* Counters: requests completed, currently admitted, queued; device bytes the
+ * server holds (its high-water mark in peak_bytes_out). */
+mps_status mps_server_stats(mps_server* srv, int64_t* completed_out, int32_t* active_out, int32_t* queued_out,
+                            size_t* bytes_out, size_t* peak_bytes_out);
+/* Stops the worker after the requests in flight finish and frees the slots. */
+void mps_server_destroy(mps_server* srv);
+
 /* Apply one two-qubit gate to two adjacent site tensors that live in the
  * caller's device memory, allocating nothing.
  *

@@ -16,6 +16,7 @@ namespace mpsv {
 
 void set_error(const char* fmt, ...);
 mps_status cuda_fail(cudaError_t e, const char* what);
+const char* last_error();
 
 #define MPSV_CUDA(call)                                   \
   do {                                                    \

@@ -1,0 +1,217 @@
+// Tensor-core GEMM for sm_103a (tcgen05, accumulator in tensor memory) with
+// FP32 accuracy from TF32 products: every FP32 operand x is split into
+// x_hi = tf32(x) and x_lo = x - x_hi, and C = A_hi B_hi + A_hi B_lo + A_lo B_hi
+// (the dropped A_lo B_lo term is below FP32 rounding).
+//
+//   C[M x N] (+)= A[M x K] * B[K x N]
+//   A row-major with leading dimension lda (K contiguous),
+//   B given as Bt[N x K] row-major with leading dimension ldb (K contiguous),
+//   C row-major with leading dimension ldc; FP32 throughout.
+//   Batched: blockIdx.z selects A + z*sA, Bt + z*sB, C + z*sC.
+//
+// One CTA computes a 128 x 128 tile with 128 threads (one warpgroup).  Per
+// 32-wide K chunk the threads stage A and B, split into hi and lo, in shared
+// memory in the canonical K-major 128-byte-swizzled layout (8-row atoms of
+// 1024 bytes; the 16-byte chunk c of row r sits at chunk c ^ (r mod 8)); one
+// elected thread issues the 4 x 3 tcgen05.mma (M 128, N 128, K 8) and
+// commits them to an mbarrier; the other threads wait with a bounded spin.
+// The epilogue reads the accumulator with tcgen05.ld (warp w owns rows
+// 32w..32w+31) and stores it.  A wait that runs out sets *err and the CTA
+// skips the rest (the accumulator is still released).
+#pragma once
+
+#include <stdint.h>
+
+namespace mpsv {
+namespace tc {
+
+constexpr int kBM = 128, kBN = 128, kBK = 32;
+constexpr int kThreads = 128;
+constexpr uint32_t kTmemCols = 128;
+constexpr int kTileBytes = kBM * kBK * 4;  // 16 KB per operand tile (hi or lo)
+constexpr long long kSpinLimit = 1ll << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// K-major SWIZZLE_128B shared-memory matrix descriptor (tcgen05): start
+// address >> 4 in bits 0-13, leading-byte offset (unused for this layout) in
+// 16-29, stride-byte offset (1024 B between 8-row atoms) >> 4 in 32-45, the
+// descriptor version 1 in bits 46-47, swizzle mode 2 (128 B) in bits 61-63.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor of kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
+// (bits 7-9 and 10-12 = 2), both K-major, N >> 3 in bits 17-22, M >> 4 in 24-28.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// byte offset of element (row, k) of a K-major 128B-swizzled tile, 0 <= k < 32
+__device__ __forceinline__ uint32_t swz_offset(int row, int k) {
+  const int chunk = (k >> 2) ^ (row & 7);
+  return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + chunk * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t r;
+  asm volatile("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Bounded wait for the phase with parity `parity` to complete; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc));
+}
+
+template <bool kAccumulate>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_tf32x3_kernel(int M, int N, int K, const float* __restrict__ A, long long lda, long long sA,
+                       const float* __restrict__ Bt, long long ldb, long long sB, float* __restrict__ C,
+                       long long ldc, long long sC, int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-aligned operand tiles: A_hi, A_lo, B_hi, B_lo
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* tA_hi = base;
+  unsigned char* tA_lo = base + kTileBytes;
+  unsigned char* tB_hi = base + 2 * kTileBytes;
+  unsigned char* tB_lo = base + 3 * kTileBytes;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_base_s;
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+  const long long z = blockIdx.z;
+  A += z * sA;
+  Bt += z * sB;
+  C += z * sC;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    s_fail = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base_s;
+  const uint32_t idesc = idesc_tf32(kBM, kBN);
+
+  uint32_t phase = 0;
+  bool ok = true;
+  const int nk = (K + kBK - 1) / kBK;
+  for (int kc = 0; kc < nk && ok; ++kc) {
+    const int k0 = kc * kBK;
+    // stage A (rows m0.., K k0..k0+31) and Bt (rows n0..) split into hi / lo
+    for (int e = tid; e < kBM * kBK; e += kThreads) {
+      const int r = e / kBK, k = e % kBK;
+      const int gr = m0 + r, gk = k0 + k;
+      const float x = (gr < M && gk < K) ? A[(long long)gr * lda + gk] : 0.f;
+      const float hi = tf32_hi(x);
+      const uint32_t off = swz_offset(r, k);
+      *reinterpret_cast<float*>(tA_hi + off) = hi;
+      *reinterpret_cast<float*>(tA_lo + off) = x - hi;
+      const int gn = n0 + r;
+      const float y = (gn < N && gk < K) ? Bt[(long long)gn * ldb + gk] : 0.f;
+      const float yh = tf32_hi(y);
+      *reinterpret_cast<float*>(tB_hi + off) = yh;
+      *reinterpret_cast<float*>(tB_lo + off) = y - yh;
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint64_t dAh = smem_desc(smem_u32(tA_hi)), dAl = smem_desc(smem_u32(tA_lo));
+      const uint64_t dBh = smem_desc(smem_u32(tB_hi)), dBl = smem_desc(smem_u32(tB_lo));
+#pragma unroll
+      for (int kk = 0; kk < kBK / 8; ++kk) {
+        const uint64_t adv = (uint64_t)((kk * 32) >> 4);  // 8 tf32 = 32 bytes along K
+        const uint32_t first = (kAccumulate || kc > 0 || kk > 0) ? 1u : 0u;
+        mma_tf32(tmem, dAh + adv, dBh + adv, idesc, first);
+        mma_tf32(tmem, dAh + adv, dBl + adv, idesc, 1u);
+        mma_tf32(tmem, dAl + adv, dBh + adv, idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&mbar)));
+    }
+    if (!mbar_wait(&mbar, phase)) {
+      s_fail = 1;
+      ok = false;
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    if (s_fail) ok = false;
+  }
+
+  if (ok) {
+    // epilogue: warp w reads accumulator rows 32w .. 32w+31
+    const int row = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < kBN; c0 += 16) {
+      uint32_t v[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (row < M) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int col = n0 + c0 + j;
+          if (col < N) {
+            const float val = __uint_as_float(v[j]);
+            float* dst = C + (long long)row * ldc + col;
+            *dst = kAccumulate ? (*dst + val) : val;
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicExch(err, 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+constexpr size_t kSmemBytes = 4 * kTileBytes + 1024;
+
+}  // namespace tc
+}  // namespace mpsv

@@ -89,6 +89,13 @@ def _load():
         "vqe_eval": ([P, P, SZ, P, P], ctypes.c_int),
         "vqe_eval_batch": ([P, SZ, P, P], ctypes.c_int),
         "vqe_eval_batch_async": ([P, SZ, P, P], ctypes.c_int),
+        "mps_server_create": ([ctypes.c_int, I32, SZ, PP], ctypes.c_int),
+        "mps_server_add_fragment": ([P, P, P, P, ctypes.POINTER(Config), ctypes.POINTER(I32)], ctypes.c_int),
+        "vqe_submit": ([P, I32, P, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+        "vqe_poll": ([P, ctypes.c_uint64, I32, ctypes.POINTER(D), ctypes.POINTER(D)], ctypes.c_int),
+        "mps_server_stats": ([P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(I32), ctypes.POINTER(I32),
+                              ctypes.POINTER(SZ), ctypes.POINTER(SZ)], ctypes.c_int),
+        "mps_server_destroy": ([P], None),
         "mps_ctx_profile": ([P, ctypes.c_uint32], ctypes.c_int),
         "mps_ctx_profile_read": ([P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                   ctypes.POINTER(D), I32], ctypes.c_int),
@@ -170,8 +177,16 @@ def template_to_abi(tmpl) -> np.ndarray:
 _live_contexts = weakref.WeakSet()
 
 
+_live_servers = weakref.WeakSet()
+
+
 @atexit.register
 def _close_all_contexts():
+    for srv in list(_live_servers):  # servers use circuits and Hamiltonians of contexts
+        try:
+            srv.close()
+        except Exception:
+            pass
     for c in list(_live_contexts):
         try:
             c.close()
@@ -443,3 +458,58 @@ def vqe_eval_batch(requests):
         _check(rc)
     del keep
     return energies, status
+
+
+class Server:
+    """Continuous-batching server of energy evaluations (vqe_submit / vqe_poll)."""
+
+    def __init__(self, device: int = 0, max_slots: int = 8, hbm_budget_bytes: int = 0):
+        h = ctypes.c_void_p()
+        _check(_lib.mps_server_create(int(device), int(max_slots), int(hbm_budget_bytes), ctypes.byref(h)))
+        self.handle = h
+        self._keep = []
+        _live_servers.add(self)
+
+    def add_fragment(self, circuit: Circuit, ham: Hamiltonian, init_bits=None, chi_max: int = 64,
+                     precision: str = "fp32", trunc_rel: float = 1e-5, svd_fp64: bool = False) -> int:
+        cfg = Config(int(chi_max), PRECISIONS[precision], float(trunc_rel), 1 if svd_fp64 else 0, 0, 0.0)
+        bits = None if init_bits is None else np.ascontiguousarray(init_bits, dtype=np.uint8)
+        out = ctypes.c_int32()
+        _check(_lib.mps_server_add_fragment(self.handle, circuit.handle, ham.handle, _ptr(bits), ctypes.byref(cfg),
+                                            ctypes.byref(out)))
+        self._keep += [circuit, ham]  # must outlive the server
+        return out.value
+
+    def submit(self, fragment: int, theta) -> int:
+        th = np.ascontiguousarray(theta, dtype=np.float64)
+        t = ctypes.c_uint64()
+        _check(_lib.vqe_submit(self.handle, int(fragment), _ptr(th), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """(energy, latency_ms), or None if not finished within timeout_ms."""
+        e, lat = ctypes.c_double(), ctypes.c_double()
+        rc = _lib.vqe_poll(self.handle, ctypes.c_uint64(ticket), int(timeout_ms), ctypes.byref(e), ctypes.byref(lat))
+        if rc == MPS_ETIMEOUT:
+            return None
+        _check(rc)
+        return e.value, lat.value
+
+    def stats(self) -> dict:
+        c, a, q = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32()
+        b, pk = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(_lib.mps_server_stats(self.handle, ctypes.byref(c), ctypes.byref(a), ctypes.byref(q), ctypes.byref(b),
+                                     ctypes.byref(pk)))
+        return {"completed": c.value, "active": a.value, "queued": q.value, "bytes": b.value,
+                "peak_bytes": pk.value}
+
+    def close(self):
+        if self.handle:
+            _lib.mps_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,74 @@
+"""Serving (vqe_submit / vqe_poll): continuous batching over resident fragments.
+
+Each request's energy is the same alone (vqe_eval) and in the mix (several
+fragments of different sizes in flight together, requests joining while
+others run); an HBM budget smaller than two evaluations admits them one at a
+time and still completes every request."""
+
+import numpy as np
+import pytest
+
+from oracle import mps as om
+from paper_2303_03681_gb300.inputs import (MASTER_SEED, brickwork_circuit, hf_bits, jw_molecular_hamiltonian,
+                                           make_rng, random_integrals, random_local_pauli_sum, uccsd_template)
+from paper_2303_03681_gb300.inputs.circuits import CircuitTemplate
+
+pytestmark = pytest.mark.gpu
+
+
+def _fragments(mps, ctx):
+    out = []
+    for k, (n_orb, n_e) in enumerate([(4, 4), (5, 4), (6, 6)]):
+        h, g = random_integrals(n_orb, make_rng(MASTER_SEED + 40 + k))
+        ham = jw_molecular_hamiltonian(h, g)
+        tmpl = uccsd_template(2 * n_orb, n_e, max_excitations=30)
+        out.append((tmpl, ham, hf_bits(2 * n_orb, n_e), 32))
+    gl = brickwork_circuit(14, 6, make_rng(MASTER_SEED + 44))
+    out.append((CircuitTemplate.from_gates(gl), random_local_pauli_sum(14, 120, make_rng(MASTER_SEED + 45)), None, 64))
+    return [(t, mps.Circuit(ctx, t), h, mps.Hamiltonian(ctx, h), b, chi) for t, h, b, chi in out]
+
+
+@pytest.mark.parametrize("budget", [0, 1])
+def test_results_same_alone_and_in_the_mix(budget):
+    from paper_2303_03681_gb300 import mps
+
+    ctx = mps.Context(0)
+    frags = _fragments(mps, ctx)
+    srv = mps.Server(0, max_slots=4, hbm_budget_bytes=budget)
+    ids = [srv.add_fragment(c, H, b, chi_max=chi, precision="fp64", trunc_rel=1e-12, svd_fp64=True)
+           for _, c, _, H, b, chi in frags]
+    rng = make_rng(MASTER_SEED + 46)
+    reqs = []
+    for k in range(16):
+        f = k % len(frags)
+        theta = rng.uniform(-0.3, 0.3, frags[f][0].n_params)
+        reqs.append((f, theta, srv.submit(ids[f], theta)))
+    got = {}
+    for f, theta, t in reqs:
+        res = srv.poll(t, timeout_ms=120000)
+        assert res is not None
+        got[t] = res
+    stats = srv.stats()
+    assert stats["completed"] == 16 and stats["active"] == 0 and stats["queued"] == 0
+    for f, theta, t in reqs:
+        tmpl, c, ham, H, bits, chi = frags[f]
+        st = mps.State(ctx, tmpl.n_qubits, bits, chi_max=chi, precision="fp64", trunc_rel=1e-12)
+        alone, status = mps.vqe_eval(ctx, [(st, c, H, theta, bits)])
+        assert status[0] == 0
+        assert got[t][0] == alone[0]
+        assert got[t][1] > 0
+    tmpl, c, ham, H, bits, chi = frags[0]
+    f, theta, t = reqs[0]
+    assert abs(got[t][0] - om.vqe_energy(tmpl, theta, bits, ham, chi_max=chi, eps_rel=1e-12)) <= 1e-10
+    srv.close()
+
+
+def test_poll_and_submit_errors():
+    from paper_2303_03681_gb300 import mps
+
+    srv = mps.Server(0, max_slots=1)
+    with pytest.raises(mps.MpsError):
+        srv.poll(12345, timeout_ms=0)
+    with pytest.raises(mps.MpsError):
+        srv.submit(0, np.zeros(1))  # no fragment registered
+    srv.close()
