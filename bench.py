@@ -276,7 +276,7 @@ def run_gpu(args):
     H = mps.Hamiltonian(ctxs[0], w["ham"])
     C = mps.Circuit(ctxs[0], w["tmpl"])
     states = [mps.State(c, w["tmpl"].n_qubits, w["bits"], chi_max=w["chi"], precision=w["precision"],
-                        trunc_rel=w["trunc"], svd_fp64=svd64) for c in ctxs]
+                        trunc_rel=w["trunc"], svd_fp64=svd64, tensor_cores=args.tensor_cores) for c in ctxs]
     n_steps = args.warmup + args.steps
     n_par = max(1, w["tmpl"].n_params)
     thetas = thetas_for(w, (n_steps + args.steps) * B, rank_seed(rank))
@@ -380,6 +380,8 @@ def run_gpu(args):
         "data": "synthetic",
         "config": dict(w["desc"], precision=f"{w['precision']} storage/contractions, {args.svd} Jacobi SVD, "
                                             f"FP64 energy sum",
+                       contractions=("tcgen05 TF32 hi/lo x3" if args.tensor_cores and w["precision"] == "fp32"
+                                     else "CUDA cores"),
                        batch=f"{B} concurrent evaluations per step (one stream each)",
                        l2="flushed between steps (256 MB write)", parallelism=f"replicas x{world}"),
         "e2e": {"value": job_throughput(args.steps * B, world, e2e_s), "unit": "evals/s",
@@ -412,7 +414,7 @@ def serve_phase(mps, device, C, H, w, args, rate):
     throughput) against a continuous-batching server with --batch slots."""
     srv = mps.Server(device, max_slots=args.batch)
     frag = srv.add_fragment(C, H, w["bits"], chi_max=w["chi"], precision=w["precision"], trunc_rel=w["trunc"],
-                            svd_fp64=(args.svd == "fp64"))
+                            svd_fp64=(args.svd == "fp64"), tensor_cores=args.tensor_cores)
     rng = make_rng(MASTER_SEED + 77)
     gaps = rng.exponential(1.0 / max(rate, 1e-6), args.serve_requests)
     thetas = thetas_for(w, args.serve_requests, MASTER_SEED + 78)
@@ -460,6 +462,8 @@ def main():
                     help="Jacobi SVD precision (default: fp64 for complex128 states, fp32 for complex64)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batch", type=int, default=1, help="concurrent evaluations per step")
+    ap.add_argument("--tensor-cores", type=int, choices=[0, 1], default=0,
+                    help="complex64 environment contractions on tcgen05 (1) or CUDA cores (0)")
     ap.add_argument("--serve-requests", type=int, default=0,
                     help="after the timed steps, serve this many Poisson-arriving requests (p50/p99 latency)")
     args = ap.parse_args()

@@ -63,6 +63,9 @@ typedef struct {
   int32_t svd_fp64;       /* 1: FP64 Jacobi SVD; 0: SVD in the storage precision */
   int32_t svd_max_sweeps; /* Jacobi sweep cap; 0 selects 60 */
   double svd_tol;         /* rotate a pair while |b_ij| > tol sqrt(b_ii b_jj); 0: default */
+  int32_t tensor_cores;   /* complex64 states: 1 = environment contractions on the tensor
+                             cores (tcgen05, TF32 hi/lo split x3, FP32 accumulation);
+                             0 = FP32 CUDA-core kernels.  Ignored for complex128. */
 } mps_config;
 
 /* One gate.  arity 1: u holds the 2x2 matrix (4 complex = 8 doubles, row

@@ -111,6 +111,8 @@ struct DevReport {
   int max_sweeps;
   long long two_qubit_gates;
   double svd_flops;
+  int tc_error;  // a tensor-core kernel ran out of its bounded wait
+  int pad;
 };
 
 // Parameters of the truncation SVD.

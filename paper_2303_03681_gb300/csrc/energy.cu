@@ -3,11 +3,13 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <unordered_map>
 
 #include "gate_kernels.cuh"
 #include "energy_kernels.cuh"
 #include "internal.h"
+#include "tc_gemm.cuh"
 
 namespace mpsv {
 
@@ -29,7 +31,8 @@ struct Node {
 // on the bond left of site s; node (parent, op) extends its parent's string by
 // one site.
 static mps_status build_trie(mps_ham* h, const uint8_t* ops, const double* coeffs, std::vector<int>& parent_src,
-                             std::vector<int2>& child, std::vector<int4>& leaf, std::vector<int2>& trace) {
+                             std::vector<int2>& child, std::vector<int4>& leaf, std::vector<int2>& trace,
+                             std::vector<int2>& dense, std::vector<int>& diag) {
   const int n = h->n;
   std::vector<Node> nodes(n);
   for (int s = 0; s < n; ++s) {
@@ -112,6 +115,17 @@ static mps_status build_trie(mps_ham* h, const uint8_t* ops, const double* coeff
           leaf.push_back(make_int4(nodes[nd.parent].entry, nd.op, t, 0));
       }
     }
+    L.off_dense = dense.size();
+    L.off_diag = diag.size();
+    for (int e = 0; e < n_entries; ++e) {
+      const int src = parent_src[L.off_parent + e];
+      if (src < 0)
+        diag.push_back(e);
+      else
+        dense.push_back(make_int2(e, src));
+    }
+    L.n_dense = (int)(dense.size() - L.off_dense);
+    L.n_diag = (int)(diag.size() - L.off_diag);
     L.n_parents = n_entries;
     L.n_children = slots;
     L.n_leaves = (int)(leaf.size() - L.off_leaf);
@@ -169,6 +183,58 @@ static mps_status ensure_env_buffers(const std::vector<int>& chi, mps_state* st,
   return MPS_OK;
 }
 
+// Tensor-core path of one level (complex64 only).  Returns false if a launch failed.
+template <typename R>
+static bool launch_env_tc(mps_state*, mps_ham*, const LevelHost&, int, const std::vector<int>&, const cplx<R>*,
+                          const cplx<R>*, cplx<R>*, cplx<R>*) {
+  return false;  // complex128 states never take this path
+}
+
+template <>
+bool launch_env_tc<float>(mps_state* st, mps_ham* h, const LevelHost& L, int j, const std::vector<int>& chi,
+                          const float2* Lprev, const float2* Bj, float2* M, float2* Lcur) {
+  // the shared-memory opt-in is a per-device function attribute
+  static std::mutex mu;
+  static uint64_t done_mask = 0;
+  mps_ctx* c = st->ctx;
+  {
+    std::lock_guard<std::mutex> g(mu);
+    const uint64_t bit = 1ull << (c->device & 63);
+    if (!(done_mask & bit)) {
+      if (cudaFuncSetAttribute(tc::cgemm_kernel<EnvMProb>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tc::kSmemBytes) != cudaSuccess ||
+          cudaFuncSetAttribute(tc::cgemm_kernel<EnvChildProb>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tc::kSmemBytes) != cudaSuccess)
+        return false;
+      done_mask |= bit;
+    }
+  }
+  cudaStream_t s = c->stream;
+  const int chi_l = chi[j], chi_r = chi[j + 1];
+  int* err = &st->d_rep->tc_error;
+  if (L.n_diag) {
+    KernelScope k(c, MPS_K_ENV_M);
+    const size_t tot = (size_t)L.n_diag * chi_l * 2 * chi_r;
+    env_m_diag_kernel<float><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(
+        h->d_diag + L.off_diag, L.n_diag, Bj, st->d_lam + st->lam_off[j], chi_l, chi_r, M);
+  }
+  if (L.n_dense) {
+    KernelScope k(c, MPS_K_ENV_M);
+    EnvMProb p{h->d_dense + L.off_dense, Lprev, Bj, M, chi_l, chi_r};
+    const int tiles_n = (2 * chi_r + tc::kBN / 2 - 1) / (tc::kBN / 2);
+    const dim3 grid((unsigned)((size_t)L.n_dense * tiles_n), (unsigned)((chi_l + tc::kBM - 1) / tc::kBM));
+    tc::cgemm_kernel<EnvMProb><<<grid, tc::kThreads, tc::kSmemBytes, s>>>(p, tiles_n, err);
+  }
+  if (L.n_children) {
+    KernelScope k(c, MPS_K_ENV_CHILD);
+    EnvChildProb p{h->d_child + L.off_child, Bj, M, Lcur, chi_l, chi_r};
+    const int tiles_n = (chi_r + tc::kBN / 2 - 1) / (tc::kBN / 2);
+    const dim3 grid((unsigned)((size_t)L.n_children * tiles_n), (unsigned)((chi_r + tc::kBM - 1) / tc::kBM));
+    tc::cgemm_kernel<EnvChildProb><<<grid, tc::kThreads, tc::kSmemBytes, s>>>(p, tiles_n, err);
+  }
+  return cudaPeekAtLastError() == cudaSuccess;
+}
+
 template <typename R>
 static mps_status energy_levels(mps_state* st, mps_ham* h, double* d_out) {
   cudaStream_t s = st->ctx->stream;
@@ -187,6 +253,7 @@ static mps_status energy_levels(mps_state* st, mps_ham* h, double* d_out) {
   if (rc != MPS_OK) return rc;
   const long long nt = h->n_terms;
   mps_ctx* c = st->ctx;
+  if (st->tc) MPSV_CUDA(cudaMemsetAsync(&st->d_rep->tc_error, 0, sizeof(int), s));
   if (nt) {
     KernelScope k(c, MPS_K_SETUP);
     fill_kernel<<<(unsigned)((nt + 255) / 256), 256, 0, s>>>(st->d_vals, nt, 1.0);
@@ -213,14 +280,23 @@ static mps_status energy_levels(mps_state* st, mps_ham* h, double* d_out) {
     lv.cap_r = chi[j + 1];
     const cplx<R>* Bj = B + st->site_off[j];
     const int tl = (lv.cap_l + kTile - 1) / kTile, tr = (lv.cap_r + kTile - 1) / kTile;
-    {
-      KernelScope k(c, MPS_K_ENV_M);
-      env_m_kernel<R><<<(unsigned)((size_t)L.n_parents * tl * tr), blk, 0, s>>>(
-          Lprev, Bj, st->d_lam + st->lam_off[j], st->d_chi, lv, M);
-    }
-    if (L.n_children) {
-      KernelScope k(c, MPS_K_ENV_CHILD);
-      env_child_kernel<R><<<(unsigned)((size_t)L.n_children * tr * tr), blk, 0, s>>>(M, Bj, st->d_chi, lv, Lcur);
+    if (st->tc) {
+      // complex64 on the tensor cores: diagonal parents by scaling, stored
+      // environments and children as batched tcgen05 complex GEMMs
+      if (!launch_env_tc<R>(st, h, L, j, chi, Lprev, Bj, M, Lcur)) {
+        set_error("energy: tensor-core launch failed: %s", cudaGetErrorString(cudaGetLastError()));
+        return MPS_ECUDA;
+      }
+    } else {
+      {
+        KernelScope k(c, MPS_K_ENV_M);
+        env_m_kernel<R><<<(unsigned)((size_t)L.n_parents * tl * tr), blk, 0, s>>>(
+            Lprev, Bj, st->d_lam + st->lam_off[j], st->d_chi, lv, M);
+      }
+      if (L.n_children) {
+        KernelScope k(c, MPS_K_ENV_CHILD);
+        env_child_kernel<R><<<(unsigned)((size_t)L.n_children * tr * tr), blk, 0, s>>>(M, Bj, st->d_chi, lv, Lcur);
+      }
     }
     if (L.n_leaves) {
       KernelScope k(c, MPS_K_ENV_LEAF);
@@ -234,7 +310,8 @@ static mps_status energy_levels(mps_state* st, mps_ham* h, double* d_out) {
   }
   {
     KernelScope k(c, MPS_K_REDUCE);
-    energy_reduce_kernel<<<1, 1024, 0, s>>>(st->d_vals, h->d_coeffs, nt, 0.0, d_out ? d_out : st->d_energy);
+    energy_reduce_kernel<<<1, 1024, 0, s>>>(st->d_vals, h->d_coeffs, nt, 0.0, st->tc ? &st->d_rep->tc_error : nullptr,
+                                            d_out ? d_out : st->d_energy);
   }
   MPSV_CUDA(cudaGetLastError());
   return MPS_OK;
@@ -259,7 +336,7 @@ static void destroy_ham(mps_ham* h) {
   DeviceGuard guard(c->device);
   cudaStreamSynchronize(c->stream);
   for (void* p : {(void*)h->d_parent_src, (void*)h->d_child, (void*)h->d_leaf, (void*)h->d_trace,
-                  (void*)h->d_coeffs})
+                  (void*)h->d_coeffs, (void*)h->d_dense, (void*)h->d_diag})
     dev_free(c, p);
   delete h;
 }
@@ -267,6 +344,20 @@ static void destroy_ham(mps_ham* h) {
 }  // namespace mpsv
 
 using namespace mpsv;
+
+// Queues a read of the tensor-core timeout flag; *flag is valid after the
+// stream synchronises.
+static cudaError_t queue_tc_flag(mps_state* st, int* flag) {
+  *flag = 0;
+  if (!st->tc) return cudaSuccess;
+  return cudaMemcpyAsync(flag, &st->d_rep->tc_error, sizeof(int), cudaMemcpyDeviceToHost, st->ctx->stream);
+}
+
+static mps_status tc_flag_status(int flag) {
+  if (!flag) return MPS_OK;
+  set_error("energy: a tensor-core contraction ran out of its bounded wait");
+  return MPS_ETIMEOUT;
+}
 
 extern "C" {
 
@@ -289,7 +380,9 @@ mps_status mps_hamiltonian_create(mps_ctx* ctx, int32_t n_qubits, size_t n_terms
   std::vector<int2> child;
   std::vector<int4> leaf;
   std::vector<int2> trace;
-  mps_status rc = build_trie(h, ops, coeffs, parent_src, child, leaf, trace);
+  std::vector<int2> dense;
+  std::vector<int> diag;
+  mps_status rc = build_trie(h, ops, coeffs, parent_src, child, leaf, trace, dense, diag);
   if (rc != MPS_OK) {
     delete h;
     return rc;
@@ -307,6 +400,8 @@ mps_status mps_hamiltonian_create(mps_ctx* ctx, int32_t n_qubits, size_t n_terms
   up((void**)&h->d_child, child.data(), child.size() * sizeof(int2));
   up((void**)&h->d_leaf, leaf.data(), leaf.size() * sizeof(int4));
   up((void**)&h->d_trace, trace.data(), trace.size() * sizeof(int2));
+  up((void**)&h->d_dense, dense.data(), dense.size() * sizeof(int2));
+  up((void**)&h->d_diag, diag.data(), diag.size() * sizeof(int));
   up((void**)&h->d_coeffs, coeffs, n_terms * sizeof(double));
   if (rc == MPS_OK) {
     cudaError_t e = cudaStreamSynchronize(ctx->stream);
@@ -352,6 +447,8 @@ mps_status mps_energy(mps_state* st, const mps_ham* h, double* energy_out, doubl
   mps_status rc = ham_energy_async(st, hh, nullptr);
   if (rc != MPS_OK) return rc;
   MPSV_CUDA(cudaMemcpyAsync(energy_out, st->d_energy, sizeof(double), cudaMemcpyDeviceToHost, st->ctx->stream));
+  int tc_flag = 0;
+  MPSV_CUDA(queue_tc_flag(st, &tc_flag));
   if (norm_out) {
     // sum of lam^2 on bond 1 (the first inner bond; bond 0 is the trivial edge)
     const int b = st->n > 1 ? 1 : 0;
@@ -368,7 +465,7 @@ mps_status mps_energy(mps_state* st, const mps_ham* h, double* energy_out, doubl
     *norm_out = s;
   }
   MPSV_CUDA(cudaStreamSynchronize(st->ctx->stream));
-  return MPS_OK;
+  return tc_flag_status(tc_flag);
 }
 
 mps_status mps_expectations(mps_state* st, const mps_ham* h, double* values_out) {
@@ -383,8 +480,10 @@ mps_status mps_expectations(mps_state* st, const mps_ham* h, double* values_out)
   if (h->n_terms)
     MPSV_CUDA(cudaMemcpyAsync(values_out, st->d_vals, h->n_terms * sizeof(double), cudaMemcpyDeviceToHost,
                               st->ctx->stream));
+  int tc_flag = 0;
+  MPSV_CUDA(queue_tc_flag(st, &tc_flag));
   MPSV_CUDA(cudaStreamSynchronize(st->ctx->stream));
-  return MPS_OK;
+  return tc_flag_status(tc_flag);
 }
 
 mps_status vqe_eval(mps_ctx* ctx, const vqe_request* reqs, size_t n, double* energies_out,
@@ -408,8 +507,10 @@ mps_status vqe_eval(mps_ctx* ctx, const vqe_request* reqs, size_t n, double* ene
     if (rc == MPS_OK) {
       cudaError_t e = cudaMemcpyAsync(&energies_out[i], r.state->d_energy, sizeof(double), cudaMemcpyDeviceToHost,
                                       ctx->stream);
+      int tc_flag = 0;
+      if (e == cudaSuccess) e = queue_tc_flag(r.state, &tc_flag);
       if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-      if (e != cudaSuccess) rc = cuda_fail(e, "vqe_eval");
+      rc = e != cudaSuccess ? cuda_fail(e, "vqe_eval") : tc_flag_status(tc_flag);
     }
     if (rc != MPS_OK) {
       energies_out[i] = 0.0;
@@ -473,6 +574,7 @@ static mps_status run_batch(const vqe_request* reqs, size_t n, double* energies_
     }
   }
   // energies (each reads its bond dimensions once), then the results
+  std::vector<int> tc_flag(n, 0);
   for (size_t i = 0; i < n; ++i) {
     if (rc[i] != MPS_OK) continue;
     const vqe_request& r = reqs[i];
@@ -481,6 +583,7 @@ static mps_status run_batch(const vqe_request* reqs, size_t n, double* energies_
     if (rc[i] == MPS_OK && !on_device) {
       cudaError_t e = cudaMemcpyAsync(&energies_out[i], r.state->d_energy, sizeof(double), cudaMemcpyDeviceToHost,
                                       r.state->ctx->stream);
+      if (e == cudaSuccess) e = queue_tc_flag(r.state, &tc_flag[i]);
       if (e != cudaSuccess) rc[i] = cuda_fail(e, "vqe_eval_batch");
     }
   }
@@ -489,7 +592,7 @@ static mps_status run_batch(const vqe_request* reqs, size_t n, double* energies_
     if (rc[i] == MPS_OK && !on_device) {
       DeviceGuard guard(reqs[i].state->ctx->device);
       cudaError_t e = cudaStreamSynchronize(reqs[i].state->ctx->stream);
-      if (e != cudaSuccess) rc[i] = cuda_fail(e, "vqe_eval_batch");
+      rc[i] = e != cudaSuccess ? cuda_fail(e, "vqe_eval_batch") : tc_flag_status(tc_flag[i]);
     }
     if (rc[i] != MPS_OK) {
       if (!on_device) energies_out[i] = 0.0;

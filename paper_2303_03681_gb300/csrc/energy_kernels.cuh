@@ -51,7 +51,8 @@ struct EnvLevel {
   int cap_l, cap_r;  // bond dimensions left / right of the site at launch (grid extents and slot strides)
 };
 
-// M^b_p[a][d] = sum_c L_p[a][c] B[c][b][d]   (b = 0, 1);  slot stride of M: 2 cap_l cap_r
+// M_p[a][b][d] = sum_c L_p[a][c] B[c][b][d]   (b = 0, 1): row-major chi_l x 2 chi_r,
+// i.e. M_p = L_p B with B viewed as chi_l x 2 chi_r; slot stride of M: 2 cap_l cap_r
 template <typename R>
 __global__ void __launch_bounds__(kTile* kTile)
     env_m_kernel(const cplx<R>* __restrict__ Lprev, const cplx<R>* __restrict__ B, const double* __restrict__ lam,
@@ -72,8 +73,8 @@ __global__ void __launch_bounds__(kTile* kTile)
     if (a < chi_l && d < chi_r) {
       const R w = R(lam[a] * lam[a]);
       const C b0 = B[(size_t)(a * 2 + 0) * chi_r + d], b1 = B[(size_t)(a * 2 + 1) * chi_r + d];
-      out[(size_t)a * chi_r + d] = cscale(b0, w);
-      out[(size_t)chi_l * chi_r + (size_t)a * chi_r + d] = cscale(b1, w);
+      out[(size_t)a * 2 * chi_r + d] = cscale(b0, w);
+      out[(size_t)a * 2 * chi_r + chi_r + d] = cscale(b1, w);
     }
     return;
   }
@@ -97,8 +98,8 @@ __global__ void __launch_bounds__(kTile* kTile)
     __syncthreads();
   }
   if (a < chi_l && d < chi_r) {
-    out[(size_t)a * chi_r + d] = acc0;
-    out[(size_t)chi_l * chi_r + (size_t)a * chi_r + d] = acc1;
+    out[(size_t)a * 2 * chi_r + d] = acc0;
+    out[(size_t)a * 2 * chi_r + chi_r + d] = acc1;
   }
 }
 
@@ -117,8 +118,8 @@ __global__ void __launch_bounds__(kTile* kTile)
   const int2 cd = lv.child[cidx];
   const PauliRow pr = pauli_row(cd.y);
   const C* Mp = M + (size_t)cd.x * 2 * lv.cap_l * lv.cap_r;
-  const C* M0 = Mp + (size_t)pr.p0 * chi_l * chi_r;  // partner of row i = 0
-  const C* M1 = Mp + (size_t)pr.p1 * chi_l * chi_r;  // partner of row i = 1
+  const C* M0 = Mp + (size_t)pr.p0 * chi_r;  // partner of row i = 0 (row stride 2 chi_r)
+  const C* M1 = Mp + (size_t)pr.p1 * chi_r;  // partner of row i = 1
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int b = b0 + ty, d = d0 + tx;
   const C zero = cmk<R>(0, 0);
@@ -132,8 +133,8 @@ __global__ void __launch_bounds__(kTile* kTile)
     sB[0][ty][tx] = okb ? B[(size_t)(a * 2 + 0) * chi_r + bb] : zero;
     sB[1][ty][tx] = okb ? B[(size_t)(a * 2 + 1) * chi_r + bb] : zero;
     const bool okm = a < chi_l && d < chi_r;
-    sM[0][ty][tx] = okm ? M0[(size_t)a * chi_r + d] : zero;
-    sM[1][ty][tx] = okm ? M1[(size_t)a * chi_r + d] : zero;
+    sM[0][ty][tx] = okm ? M0[(size_t)a * 2 * chi_r + d] : zero;
+    sM[1][ty][tx] = okm ? M1[(size_t)a * 2 * chi_r + d] : zero;
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < kTile; ++kk) {
@@ -161,14 +162,14 @@ __global__ void env_leaf_kernel(const cplx<R>* __restrict__ M, const cplx<R>* __
   const int4 lf = lv.leaf[w];
   const PauliRow pr = pauli_row(lf.y);
   const C* Mp = M + (size_t)lf.x * 2 * lv.cap_l * lv.cap_r;
-  const C* Mi0 = Mp + (size_t)pr.p0 * chi_l * chi_r;
-  const C* Mi1 = Mp + (size_t)pr.p1 * chi_l * chi_r;
+  const C* Mi0 = Mp + (size_t)pr.p0 * chi_r;  // row stride 2 chi_r
+  const C* Mi1 = Mp + (size_t)pr.p1 * chi_r;
   double2 s0 = make_double2(0, 0), s1 = make_double2(0, 0);
   const int tot = chi_l * chi_r;
   for (int t = lane; t < tot; t += 32) {
     const int a = t / chi_r, b = t % chi_r;
     const C x0 = B[(size_t)(a * 2 + 0) * chi_r + b], x1 = B[(size_t)(a * 2 + 1) * chi_r + b];
-    const C y0 = Mi0[t], y1 = Mi1[t];
+    const C y0 = Mi0[(size_t)a * 2 * chi_r + b], y1 = Mi1[(size_t)a * 2 * chi_r + b];
     const double2 p0 = ccast<double2>(cmulc(x0, y0)), p1 = ccast<double2>(cmulc(x1, y1));
     s0.x += p0.x; s0.y += p0.y;
     s1.x += p1.x; s1.y += p1.y;
@@ -199,8 +200,10 @@ __global__ void env_trace_kernel(const cplx<R>* __restrict__ Lcur, const int* __
 
 // E = constant + sum_k c_k vals[k] (terms with an empty support keep vals = 1).
 // One block of 1024 threads; fixed summation order.
+// A set *err (a tensor-core contraction gave up waiting) turns the energy into NaN.
 static __global__ void energy_reduce_kernel(const double* __restrict__ vals, const double* __restrict__ coeffs,
-                                            long long n_terms, double constant, double* __restrict__ out) {
+                                            long long n_terms, double constant, const int* __restrict__ err,
+                                            double* __restrict__ out) {
   __shared__ double part[32];
   double s = 0.0;
   for (long long k = threadIdx.x; k < n_terms; k += blockDim.x) s += coeffs[k] * vals[k];
@@ -210,13 +213,85 @@ static __global__ void energy_reduce_kernel(const double* __restrict__ vals, con
   if (threadIdx.x < 32) {
     double v = threadIdx.x < (blockDim.x >> 5) ? part[threadIdx.x] : 0.0;
     v = warp_sum(v);
-    if (threadIdx.x == 0) *out = constant + v;
+    if (threadIdx.x == 0) *out = (err && *err) ? __longlong_as_double(0x7ff8000000000000ll) : constant + v;
   }
 }
 
 static __global__ void fill_kernel(double* __restrict__ p, long long n, double v) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < n) p[t] = v;
+}
+
+// ---------------------------------------------------------------------------
+// tensor-core forms (complex64 states): the same products as env_m_kernel and
+// env_child_kernel, as problems of tc::cgemm_kernel
+// ---------------------------------------------------------------------------
+
+// M_p = L_src B_j for the parents whose environment is a stored matrix;
+// list[z] = (parent entry p, environment slot src).
+struct EnvMProb {
+  const int2* list;
+  const float2* Lprev;
+  const float2* B;
+  float2* M;
+  int chi_l, chi_r;
+  __device__ __forceinline__ void dims(int, int& m, int& n, int& k) const {
+    m = chi_l;
+    n = 2 * chi_r;
+    k = chi_l;
+  }
+  __device__ __forceinline__ float2 a(int z, int row, int kk) const {
+    return Lprev[(size_t)list[z].y * chi_l * chi_l + (size_t)row * chi_l + kk];
+  }
+  __device__ __forceinline__ float2 b(int, int kk, int col) const { return B[(size_t)kk * 2 * chi_r + col]; }
+  __device__ __forceinline__ void store(int z, int row, int col, float2 v) const {
+    M[(size_t)list[z].x * 2 * chi_l * chi_r + (size_t)row * 2 * chi_r + col] = v;
+  }
+};
+
+// L_c[b][d] = sum_{i, a} ph_i conj(B[a][i][b]) M_p[a][pi(i)][d]; K runs over (i, a).
+struct EnvChildProb {
+  const int2* child;  // (parent entry, op)
+  const float2* B;
+  const float2* M;
+  float2* Lcur;
+  int chi_l, chi_r;
+  __device__ __forceinline__ void dims(int, int& m, int& n, int& k) const {
+    m = chi_r;
+    n = chi_r;
+    k = 2 * chi_l;
+  }
+  __device__ __forceinline__ float2 a(int z, int row, int kk) const {
+    const int i = kk >= chi_l ? 1 : 0, aa = kk - i * chi_l;
+    const PauliRow pr = pauli_row(child[z].y);
+    const double2 ph = i ? pr.ph1 : pr.ph0;
+    const float2 x = B[(size_t)(aa * 2 + i) * chi_r + row];  // conj(x) * ph
+    return make_float2(float(ph.x) * x.x + float(ph.y) * x.y, float(ph.y) * x.x - float(ph.x) * x.y);
+  }
+  __device__ __forceinline__ float2 b(int z, int kk, int col) const {
+    const int i = kk >= chi_l ? 1 : 0, aa = kk - i * chi_l;
+    const int2 cd = child[z];
+    const PauliRow pr = pauli_row(cd.y);
+    const int pi = i ? pr.p1 : pr.p0;
+    return M[(size_t)cd.x * 2 * chi_l * chi_r + (size_t)aa * 2 * chi_r + (size_t)pi * chi_r + col];
+  }
+  __device__ __forceinline__ void store(int z, int row, int col, float2 v) const {
+    Lcur[(size_t)z * chi_r * chi_r + (size_t)row * chi_r + col] = v;
+  }
+};
+
+// M_p = diag(lam^2) B for the parents that start strings at this site; list[z] = entry p.
+template <typename R>
+__global__ void env_m_diag_kernel(const int* __restrict__ list, int n, const cplx<R>* __restrict__ B,
+                                  const double* __restrict__ lam, int chi_l, int chi_r, cplx<R>* __restrict__ M) {
+  const size_t per = (size_t)chi_l * 2 * chi_r;
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= per * n) return;
+  const int z = (int)(t / per);
+  const size_t e = t % per;
+  const int a = (int)(e / (2 * chi_r));
+  const R w = R(lam[a] * lam[a]);
+  M[(size_t)list[z] * per + e] = cscale(B[e], w);
 }
 
 }  // namespace mpsv

@@ -49,6 +49,7 @@ __global__ void reset_kernel(cplx<R>* __restrict__ B, const size_t* __restrict__
     rep->max_sweeps = 0;
     rep->two_qubit_gates = 0;
     rep->svd_flops = 0.0;
+    rep->tc_error = 0;
   }
 }
 

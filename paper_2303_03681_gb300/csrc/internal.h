@@ -81,6 +81,7 @@ struct mps_state {
   mps_config cfg{};
   bool fp32 = false;   // complex64 storage
   bool svd64 = true;   // FP64 Jacobi
+  bool tc = false;     // tensor-core environment contractions (complex64 states)
   std::vector<int> cap;          // bond capacities, n + 1
   std::vector<size_t> site_off;  // complex elements
   std::vector<size_t> lam_off;   // doubles
@@ -127,6 +128,8 @@ namespace mpsv {
 struct LevelHost {
   int n_parents = 0, n_children = 0, n_leaves = 0, n_traces = 0;
   size_t off_parent = 0, off_child = 0, off_leaf = 0, off_trace = 0;
+  int n_dense = 0, n_diag = 0;  // parents with a stored environment / starting strings here
+  size_t off_dense = 0, off_diag = 0;
 };
 }  // namespace mpsv
 
@@ -141,6 +144,8 @@ struct mps_ham {
   int2* d_child = nullptr;
   int4* d_leaf = nullptr;
   int2* d_trace = nullptr;
+  int2* d_dense = nullptr;  // (parent entry, environment slot)
+  int* d_diag = nullptr;    // parent entry
   double* d_coeffs = nullptr;
 };
 

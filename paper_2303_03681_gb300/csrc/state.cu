@@ -498,6 +498,7 @@ mps_status mps_create(mps_ctx* ctx, int32_t n_qubits, const uint8_t* init_bits, 
   st->cfg = *cfg;
   st->fp32 = cfg->precision == MPS_PREC_FP32;
   st->svd64 = cfg->svd_fp64 != 0;
+  st->tc = st->fp32 && cfg->tensor_cores != 0;
   const int n = n_qubits;
   st->cap.resize(n + 1);
   for (int b = 0; b <= n; ++b) st->cap[b] = bond_cap(b, n, cfg->chi_max);

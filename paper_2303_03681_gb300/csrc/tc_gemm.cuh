@@ -1,23 +1,18 @@
-// Tensor-core GEMM for sm_103a (tcgen05, accumulator in tensor memory) with
-// FP32 accuracy from TF32 products: every FP32 operand x is split into
-// x_hi = tf32(x) and x_lo = x - x_hi, and C = A_hi B_hi + A_hi B_lo + A_lo B_hi
-// (the dropped A_lo B_lo term is below FP32 rounding).
+// Tensor-core complex GEMM for sm_103a (tcgen05, accumulator in tensor
+// memory) with FP32 accuracy from TF32 products: every FP32 operand value x is
+// split into x_hi = tf32(x) and x_lo = x - x_hi, and each real product is
+// A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped A_lo B_lo is below FP32
+// rounding).
 //
-//   C[M x N] (+)= A[M x K] * B[K x N]
-//   A row-major with leading dimension lda (K contiguous),
-//   B given as Bt[N x K] row-major with leading dimension ldb (K contiguous),
-//   C row-major with leading dimension ldc; FP32 throughout.
-//   Batched: blockIdx.z selects A + z*sA, Bt + z*sB, C + z*sC.
-//
-// One CTA computes a 128 x 128 tile with 128 threads (one warpgroup).  Per
-// 32-wide K chunk the threads stage A and B, split into hi and lo, in shared
-// memory in the canonical K-major 128-byte-swizzled layout (8-row atoms of
-// 1024 bytes; the 16-byte chunk c of row r sits at chunk c ^ (r mod 8)); one
-// elected thread issues the 4 x 3 tcgen05.mma (M 128, N 128, K 8) and
-// commits them to an mbarrier; the other threads wait with a bounded spin.
+// One CTA of 128 threads (one warpgroup) computes a 128 x 128 real tile.  Per
+// 32-wide real K chunk the threads stage A and B^T, split into hi and lo, in
+// shared memory in the canonical K-major 128-byte-swizzled layout (8-row
+// atoms of 1024 bytes; the 16-byte chunk c of row r sits at chunk c ^ (r mod
+// 8)); one thread issues the 4 x 3 tcgen05.mma (M 128, N 128, K 8) and
+// commits them to an mbarrier that every thread waits on with a bounded spin.
 // The epilogue reads the accumulator with tcgen05.ld (warp w owns rows
-// 32w..32w+31) and stores it.  A wait that runs out sets *err and the CTA
-// skips the rest (the accumulator is still released).
+// 32w..32w+31).  A wait that runs out sets *err; the accumulator is released
+// in every case.
 #pragma once
 
 #include <stdint.h>
@@ -30,6 +25,7 @@ constexpr int kThreads = 128;
 constexpr uint32_t kTmemCols = 128;
 constexpr int kTileBytes = kBM * kBK * 4;  // 16 KB per operand tile (hi or lo)
 constexpr long long kSpinLimit = 1ll << 26;
+constexpr uint64_t kWaitNs = 2000000000ull;  // 2 s: a tile's MMAs take microseconds
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -71,9 +67,17 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-// Bounded wait for the phase with parity `parity` to complete; false if the limit ran out.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the phase with parity `parity` to complete; false once
+// kWaitNs nanoseconds (or kSpinLimit polls) have passed without it.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   const uint32_t a = smem_u32(bar);
+  const uint64_t t0 = global_ns();
   for (long long i = 0; i < kSpinLimit; ++i) {
     uint32_t done;
     asm volatile(
@@ -82,6 +86,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((i & 255) == 255 && global_ns() - t0 > kWaitNs) return false;
   }
   return false;
 }
@@ -93,14 +98,20 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t 
       "l"(da), "l"(db), "r"(idesc), "r"(acc));
 }
 
-template <bool kAccumulate>
-__global__ void __launch_bounds__(kThreads, 1)
-    gemm_tf32x3_kernel(int M, int N, int K, const float* __restrict__ A, long long lda, long long sA,
-                       const float* __restrict__ Bt, long long ldb, long long sB, float* __restrict__ C,
-                       long long ldc, long long sC, int* __restrict__ err) {
+// Complex GEMM on the tensor cores.  For problem z the product is
+// C[m][n] = sum_k a(z, m, k) b(z, k, n) (complex FP32, M x N x K from
+// prob.dims), computed as the real GEMM C_r = A_r B_r with A_r[m][2k + t] =
+// (Re, Im)_t of a and B_r the 2 x 2 real embedding [[Re b, Im b], [-Im b,
+// Re b]] of each b, so C_r[m][2n + u] = (Re, Im)_u of C.  A CTA computes 128
+// rows x 64 complex columns; blockIdx.x = z * tiles_n + n-tile, blockIdx.y =
+// m-tile.  The loaders of Prob give a() and b() for any stored layout
+// (transposes, conjugation and phases included), so no operand is copied
+// into an intermediate layout in global memory.
+template <class Prob>
+__global__ void __launch_bounds__(kThreads, 1) cgemm_kernel(Prob prob, int tiles_n, int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-aligned operand tiles: A_hi, A_lo, B_hi, B_lo
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* tA_hi = base;
   unsigned char* tA_lo = base + kTileBytes;
   unsigned char* tB_hi = base + 2 * kTileBytes;
@@ -109,13 +120,14 @@ __global__ void __launch_bounds__(kThreads, 1)
   __shared__ uint32_t tmem_base_s;
   __shared__ int s_fail;
 
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
-  const long long z = blockIdx.z;
-  A += z * sA;
-  Bt += z * sB;
-  C += z * sC;
+  const int z = blockIdx.x / tiles_n;
+  const int nt = blockIdx.x % tiles_n;
+  int M, N, K;
+  prob.dims(z, M, N, K);
+  const int m0 = blockIdx.y * kBM, n0 = nt * (kBN / 2);
+  if (m0 >= M || n0 >= N || K <= 0) return;  // the whole CTA, before any tensor-memory use
 
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
                  "r"(kTmemCols));
@@ -131,26 +143,44 @@ __global__ void __launch_bounds__(kThreads, 1)
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base_s;
   const uint32_t idesc = idesc_tf32(kBM, kBN);
+  constexpr int kKC = kBK / 2;  // complex K per chunk
 
   uint32_t phase = 0;
   bool ok = true;
-  const int nk = (K + kBK - 1) / kBK;
+  const int nk = (K + kKC - 1) / kKC;
   for (int kc = 0; kc < nk && ok; ++kc) {
-    const int k0 = kc * kBK;
-    // stage A (rows m0.., K k0..k0+31) and Bt (rows n0..) split into hi / lo
-    for (int e = tid; e < kBM * kBK; e += kThreads) {
-      const int r = e / kBK, k = e % kBK;
-      const int gr = m0 + r, gk = k0 + k;
-      const float x = (gr < M && gk < K) ? A[(long long)gr * lda + gk] : 0.f;
-      const float hi = tf32_hi(x);
-      const uint32_t off = swz_offset(r, k);
-      *reinterpret_cast<float*>(tA_hi + off) = hi;
-      *reinterpret_cast<float*>(tA_lo + off) = x - hi;
-      const int gn = n0 + r;
-      const float y = (gn < N && gk < K) ? Bt[(long long)gn * ldb + gk] : 0.f;
-      const float yh = tf32_hi(y);
-      *reinterpret_cast<float*>(tB_hi + off) = yh;
-      *reinterpret_cast<float*>(tB_lo + off) = y - yh;
+    const int k0 = kc * kKC;
+    // A: 128 rows x 16 complex -> real columns (2k, 2k + 1) = (Re, Im)
+    for (int e = tid; e < kBM * kKC; e += kThreads) {
+      const int r = e / kKC, kk = e % kKC;
+      const int gm = m0 + r, gk = k0 + kk;
+      float2 v = make_float2(0.f, 0.f);
+      if (gm < M && gk < K) v = prob.a(z, gm, gk);
+      const float rh = tf32_hi(v.x), ih = tf32_hi(v.y);
+      const uint32_t o0 = swz_offset(r, 2 * kk), o1 = swz_offset(r, 2 * kk + 1);
+      *reinterpret_cast<float*>(tA_hi + o0) = rh;
+      *reinterpret_cast<float*>(tA_lo + o0) = v.x - rh;
+      *reinterpret_cast<float*>(tA_hi + o1) = ih;
+      *reinterpret_cast<float*>(tA_lo + o1) = v.y - ih;
+    }
+    // B^T: 64 complex columns n x 16 complex k -> 2 x 2 real blocks
+    for (int e = tid; e < (kBN / 2) * kKC; e += kThreads) {
+      const int nn = e / kKC, kk = e % kKC;
+      const int gn = n0 + nn, gk = k0 + kk;
+      float2 v = make_float2(0.f, 0.f);
+      if (gn < N && gk < K) v = prob.b(z, gk, gn);
+      const float rh = tf32_hi(v.x), ih = tf32_hi(v.y), nih = -ih;
+      const float rl = v.x - rh, il = v.y - ih;
+      const uint32_t o00 = swz_offset(2 * nn, 2 * kk), o01 = swz_offset(2 * nn, 2 * kk + 1);
+      const uint32_t o10 = swz_offset(2 * nn + 1, 2 * kk), o11 = swz_offset(2 * nn + 1, 2 * kk + 1);
+      *reinterpret_cast<float*>(tB_hi + o00) = rh;
+      *reinterpret_cast<float*>(tB_lo + o00) = rl;
+      *reinterpret_cast<float*>(tB_hi + o01) = nih;
+      *reinterpret_cast<float*>(tB_lo + o01) = -il;
+      *reinterpret_cast<float*>(tB_hi + o10) = ih;
+      *reinterpret_cast<float*>(tB_lo + o10) = il;
+      *reinterpret_cast<float*>(tB_hi + o11) = rh;
+      *reinterpret_cast<float*>(tB_lo + o11) = rl;
     }
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
@@ -159,20 +189,16 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint64_t dAh = smem_desc(smem_u32(tA_hi)), dAl = smem_desc(smem_u32(tA_lo));
       const uint64_t dBh = smem_desc(smem_u32(tB_hi)), dBl = smem_desc(smem_u32(tB_lo));
 #pragma unroll
-      for (int kk = 0; kk < kBK / 8; ++kk) {
-        const uint64_t adv = (uint64_t)((kk * 32) >> 4);  // 8 tf32 = 32 bytes along K
-        const uint32_t first = (kAccumulate || kc > 0 || kk > 0) ? 1u : 0u;
-        mma_tf32(tmem, dAh + adv, dBh + adv, idesc, first);
+      for (int ks = 0; ks < kBK / 8; ++ks) {
+        const uint64_t adv = (uint64_t)((ks * 32) >> 4);  // 8 tf32 = 32 bytes along K
+        mma_tf32(tmem, dAh + adv, dBh + adv, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
         mma_tf32(tmem, dAh + adv, dBl + adv, idesc, 1u);
         mma_tf32(tmem, dAl + adv, dBh + adv, idesc, 1u);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&mbar)));
     }
-    if (!mbar_wait(&mbar, phase)) {
-      s_fail = 1;
-      ok = false;
-    }
+    if (!mbar_wait(&mbar, phase)) s_fail = 1;
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
@@ -180,8 +206,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 
   if (ok) {
-    // epilogue: warp w reads accumulator rows 32w .. 32w+31
-    const int row = m0 + warp * 32 + lane;
+    const int row = m0 + warp * 32 + lane;  // warp w reads accumulator rows 32w .. 32w+31
     for (int c0 = 0; c0 < kBN; c0 += 16) {
       uint32_t v[16];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
@@ -193,13 +218,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (row < M) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int col = n0 + c0 + j;
-          if (col < N) {
-            const float val = __uint_as_float(v[j]);
-            float* dst = C + (long long)row * ldc + col;
-            *dst = kAccumulate ? (*dst + val) : val;
-          }
+        for (int j = 0; j < 8; ++j) {
+          const int col = n0 + c0 / 2 + j;
+          if (col < N) prob.store(z, row, col, make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])));
         }
       }
     }

@@ -36,7 +36,8 @@ class MpsError(RuntimeError):
 
 class Config(ctypes.Structure):
     _fields_ = [("chi_max", ctypes.c_int32), ("precision", ctypes.c_int32), ("trunc_rel", ctypes.c_double),
-                ("svd_fp64", ctypes.c_int32), ("svd_max_sweeps", ctypes.c_int32), ("svd_tol", ctypes.c_double)]
+                ("svd_fp64", ctypes.c_int32), ("svd_max_sweeps", ctypes.c_int32), ("svd_tol", ctypes.c_double),
+                ("tensor_cores", ctypes.c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -316,11 +317,12 @@ class State(_Child):
     _destroy = staticmethod(lambda h: _lib.mps_destroy(h))
 
     def __init__(self, ctx: Context, n_qubits: int, init_bits=None, chi_max: int = 64, precision: str = "fp64",
-                 trunc_rel: float = 0.0, svd_fp64: bool = True, svd_max_sweeps: int = 0, svd_tol: float = 0.0):
+                 trunc_rel: float = 0.0, svd_fp64: bool = True, svd_max_sweeps: int = 0, svd_tol: float = 0.0,
+                 tensor_cores: bool = False):
         self._adopt(ctx)
         self.n = int(n_qubits)
         self.cfg = Config(int(chi_max), PRECISIONS[precision], float(trunc_rel), 1 if svd_fp64 else 0,
-                          int(svd_max_sweeps), float(svd_tol))
+                          int(svd_max_sweeps), float(svd_tol), 1 if tensor_cores else 0)
         bits = None if init_bits is None else np.ascontiguousarray(init_bits, dtype=np.uint8)
         h = ctypes.c_void_p()
         _check(_lib.mps_create(ctx.handle, self.n, _ptr(bits), ctypes.byref(self.cfg), ctypes.byref(h)))
@@ -471,8 +473,10 @@ class Server:
         _live_servers.add(self)
 
     def add_fragment(self, circuit: Circuit, ham: Hamiltonian, init_bits=None, chi_max: int = 64,
-                     precision: str = "fp32", trunc_rel: float = 1e-5, svd_fp64: bool = False) -> int:
-        cfg = Config(int(chi_max), PRECISIONS[precision], float(trunc_rel), 1 if svd_fp64 else 0, 0, 0.0)
+                     precision: str = "fp32", trunc_rel: float = 1e-5, svd_fp64: bool = False,
+                     tensor_cores: bool = False) -> int:
+        cfg = Config(int(chi_max), PRECISIONS[precision], float(trunc_rel), 1 if svd_fp64 else 0, 0, 0.0,
+                     1 if tensor_cores else 0)
         bits = None if init_bits is None else np.ascontiguousarray(init_bits, dtype=np.uint8)
         out = ctypes.c_int32()
         _check(_lib.mps_server_add_fragment(self.handle, circuit.handle, ham.handle, _ptr(bits), ctypes.byref(cfg),
