@@ -380,7 +380,7 @@ def run_gpu(args):
         "data": "synthetic",
         "config": dict(w["desc"], precision=f"{w['precision']} storage/contractions, {args.svd} Jacobi SVD, "
                                             f"FP64 energy sum",
-                       contractions=("tcgen05 TF32 hi/lo x3" if args.tensor_cores and w["precision"] == "fp32"
+                       contractions=("tcgen05 TF32 hi/lo split, 4 products" if args.tensor_cores and w["precision"] == "fp32"
                                      else "CUDA cores"),
                        batch=f"{B} concurrent evaluations per step (one stream each)",
                        l2="flushed between steps (256 MB write)", parallelism=f"replicas x{world}"),

@@ -60,11 +60,16 @@ typedef struct {
   int32_t chi_max;        /* bond-dimension cap (>= 1) */
   int32_t precision;      /* mps_precision */
   double trunc_rel;       /* keep s_i > trunc_rel * s_1 (0: keep all nonzero) */
-  int32_t svd_fp64;       /* 1: FP64 Jacobi SVD; 0: SVD in the storage precision */
+  int32_t svd_fp64;       /* 0: Jacobi SVD in the storage precision;
+                             1: FP64-accurate Jacobi SVD (for complex64 states with 96 or more
+                                theta columns: FP32 sweeps to FP32 convergence, one FP64
+                                re-orthonormalisation of V, A = C~ V rebuilt in FP64, FP64 sweeps
+                                to the FP64 stopping rule);
+                             2: every Jacobi sweep in FP64 */
   int32_t svd_max_sweeps; /* Jacobi sweep cap; 0 selects 60 */
   double svd_tol;         /* rotate a pair while |b_ij| > tol sqrt(b_ii b_jj); 0: default */
   int32_t tensor_cores;   /* complex64 states: 1 = environment contractions on the tensor
-                             cores (tcgen05, TF32 hi/lo split x3, FP32 accumulation);
+                             cores (tcgen05, TF32 hi/lo split, 4 products, FP32 accumulation);
                              0 = FP32 CUDA-core kernels.  Ignored for complex128. */
 } mps_config;
 
@@ -100,6 +105,11 @@ typedef struct {
   int32_t max_sweeps_used;  /* largest number of Jacobi sweeps of one SVD */
   int64_t two_qubit_gates;  /* two-qubit gates applied */
   double svd_flops;         /* real flops of the Jacobi sweeps run (dots + rotations) */
+  int64_t svd_sweeps_fp32;  /* Jacobi sweeps run in FP32, summed over SVDs */
+  int64_t svd_sweeps_fp64;  /* Jacobi sweeps run in FP64, summed over SVDs */
+  double svd_phase_cycles[4]; /* SM clock cycles of the cluster SVDs (first CTA), summed: column
+                                 load, FP32 sweeps, FP64 re-orthonormalisation of V and A = C~ V,
+                                 FP64 sweeps with the truncation and output */
 } mps_report;
 
 /* Kernel classes for mps_ctx_profile_read. */

@@ -113,6 +113,8 @@ struct DevReport {
   double svd_flops;
   int tc_error;  // a tensor-core kernel ran out of its bounded wait
   int pad;
+  long long sweeps_fp32, sweeps_fp64;  // Jacobi sweeps run, summed over SVDs
+  double phase_cycles[4];              // cluster SVD phases (CTA 0 clock): load, FP32 sweeps, V / A rebuild, FP64 sweeps + output
 };
 
 // Parameters of the truncation SVD.
@@ -121,6 +123,59 @@ struct SvdParams {
   int max_sweeps;
   double trunc_rel;
   double tol;  // <= 0: default
+  int mixed;   // FP64 SVD of a complex64 state: FP32 sweeps, then FP64 ones (cluster kernel)
 };
+
+
+// Rotation of a column pair of the one-sided Jacobi SVD from its Gram entries
+// alpha = a_i^H a_i, beta = a_j^H a_j, g = gr + i gi = a_i^H a_j (Algorithm 1
+// of the paper, with the phase of g moved onto column j): the new columns are
+// a_i' = c a_i - conj(s e^{i phi}) a_j and a_j' = c a_j + s e^{i phi} a_i.
+// Returns false when the pair is left alone (already orthogonal to tol, or a
+// column at the rounding floor).
+template <typename S>
+__device__ __forceinline__ bool jacobi_rotation(S alpha, S beta, S gr, S gi, S tol, S floor, S tiny, S& c,
+                                                cplx<S>& sph) {
+  const S mag = sqrt(gr * gr + gi * gi);
+  if (!(mag > tiny) || !(mag > tol * sqrt(alpha * beta)) || !(min(alpha, beta) > floor)) return false;
+  const S zeta = (beta - alpha) / (S(2) * mag);
+  const S t = (zeta >= S(0) ? S(1) : S(-1)) / (fabs(zeta) + sqrt(S(1) + zeta * zeta));
+  c = S(1) / sqrt(S(1) + t * t);
+  const S s = t * c;
+  sph = cmk<S>(s * gr / mag, s * gi / mag);  // s e^{i phi}
+  return true;
+}
+
+// FP64 form.  FP64 square roots and divisions cost dozens of instructions on
+// an SM with two FP64 FMA units, so the angle is found in FP32 on Gram
+// entries scaled by a power of two near |g|, and (c, s e^{i phi}) is then
+// brought to unit norm in FP64 by c^2 + |s|^2 = 1 + d -> scale by
+// 1 - d/2 + 3 d^2 / 8 (|d| ~ 1e-7, so the rotation is unitary to FP64
+// rounding).  The angle itself is only FP32-accurate, which costs at most
+// an extra sweep: a pair left with |g| ~ 1e-7 |g| is rotated again.
+template <>
+__device__ __forceinline__ bool jacobi_rotation<double>(double alpha, double beta, double gr, double gi, double tol,
+                                                        double floor, double tiny, double& c, cplx<double>& sph) {
+  const double mag2 = gr * gr + gi * gi;
+  if (!(mag2 > tiny) || !(mag2 > tol * tol * alpha * beta) || !(min(alpha, beta) > floor)) return false;
+  // 2^-h with 2^(2h) ~ mag2 (mag2 is a normal double here)
+  const long long e2 = ((__double_as_longlong(mag2) >> 52) & 0x7ff) - 1023;
+  const long long h = e2 >> 1;
+  const double scl = __longlong_as_double((1023 - h) << 52);
+  const float xr = float(gr * scl), xi = float(gi * scl);
+  const float magf = sqrtf(xr * xr + xi * xi);
+  const float zeta = float((beta - alpha) * scl) / (2.f * magf);
+  if (!(fabsf(zeta) < 3e38f)) return false;
+  const float t = fabsf(zeta) > 1e15f ? 0.5f / zeta
+                                       : (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
+  const float cf = rsqrtf(1.f + t * t);
+  const float sf = t * cf / magf;
+  const double cd = cf, sr = double(sf) * double(xr), si = double(sf) * double(xi);
+  const double d = fma(cd, cd, fma(sr, sr, fma(si, si, -1.0)));
+  const double f = fma(d, fma(0.375, d, -0.5), 1.0);
+  c = cd * f;
+  sph = cmk<double>(sr * f, si * f);
+  return true;
+}
 
 }  // namespace mpsv

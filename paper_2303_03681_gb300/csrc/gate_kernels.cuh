@@ -50,6 +50,8 @@ __global__ void reset_kernel(cplx<R>* __restrict__ B, const size_t* __restrict__
     rep->two_qubit_gates = 0;
     rep->svd_flops = 0.0;
     rep->tc_error = 0;
+    rep->sweeps_fp32 = rep->sweeps_fp64 = 0;
+    for (int i = 0; i < 4; ++i) rep->phase_cycles[i] = 0.0;
   }
 }
 
@@ -187,15 +189,10 @@ __device__ int jacobi_sweeps(cplx<S>* A, cplx<S>* V, int m, int n, int max_sweep
         beta = warp_sum(beta);
         gam.x = warp_sum(gam.x);
         gam.y = warp_sum(gam.y);
-        const S mag = sqrt(gam.x * gam.x + gam.y * gam.y);
-        if (!(mag > tiny) || !(mag > tol * sqrt(alpha * beta)) || !(min(alpha, beta) > floor)) continue;
+        S c;
+        C sph;  // s e^{i phi}
+        if (!jacobi_rotation<S>(alpha, beta, gam.x, gam.y, tol, floor, tiny, c, sph)) continue;
         rotated = true;
-        const C ph = cmk<S>(gam.x / mag, gam.y / mag);
-        const S zeta = (beta - alpha) / (S(2) * mag);
-        const S t = (zeta >= S(0) ? S(1) : S(-1)) / (fabs(zeta) + sqrt(S(1) + zeta * zeta));
-        const S c = S(1) / sqrt(S(1) + t * t);
-        const S s = t * c;
-        const C sph = cmk<S>(s * ph.x, s * ph.y);  // s e^{i phi}
         for (int row = lane; row < m; row += 32) {
           const C x = ai[row], y = aj[row];
           C ni = cmk<S>(c * x.x, c * x.y);
@@ -333,6 +330,7 @@ __global__ void __launch_bounds__(1024, 1)
     // per sweep and column pair: three dot products over m rows (16 m flops)
     // and one rotation of the A and V columns (12 (m + n) flops)
     rep->svd_flops += (double)min(sweeps, p.max_sweeps) * 0.5 * n * (n - 1) * (16.0 * m + 12.0 * (m + n));
+    (sizeof(S) == 8 ? rep->sweeps_fp64 : rep->sweeps_fp32) += min(sweeps, p.max_sweeps);
     rep->inv_norm = 1.0 / nrm;
     chi[q + 1] = k;
   }

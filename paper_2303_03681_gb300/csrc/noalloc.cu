@@ -84,6 +84,9 @@ __global__ void noalloc_setup_kernel(unsigned char* scratch, int chi_l, int chi_
     r->max_sweeps = 0;
     r->two_qubit_gates = 0;
     r->svd_flops = 0.0;
+    r->tc_error = 0;
+    r->sweeps_fp32 = r->sweeps_fp64 = 0;
+    for (int i = 0; i < 4; ++i) r->phase_cycles[i] = 0.0;
   }
   DevGate* d = reinterpret_cast<DevGate*>(scratch + kOffGate);
   if (threadIdx.x < 16) d->u[threadIdx.x] = g.u[threadIdx.x];
@@ -146,6 +149,7 @@ extern "C" mps_status mps_gate2_noalloc(int device, void* cuda_stream, int32_t c
   p.max_sweeps = 60;
   p.trunc_rel = trunc_rel;
   p.tol = 0.0;
+  p.mixed = 0;
   const int n = 2 * chi_r, m = 2 * chi_l;
   const size_t smem = ((size_t)m * n + (size_t)n * n) * sizeof(double2) + (size_t)n * (sizeof(double) + sizeof(int)) + 64;
   svd_truncate_kernel<double, double><<<1, 32 * std::min(32, std::max(1, n / 2)), smem, s>>>(

@@ -136,13 +136,24 @@ template <typename S, typename R> static void svd_set_attr() {
   });
 }
 
-// Cluster size for the Jacobi SVD of a theta with up to mcap rows and ncap
-// columns (A = C~, stacked columns [A; V] of length mcap + ncap), or 0 when
-// the single-CTA kernel is used.
-template <typename S, typename R> static int cluster_svd_size(int mcap, int ncap) {
+// Launch plan of the cluster Jacobi SVD for a theta with up to mcap rows and
+// ncap columns (A = C~, stacked columns [A; V] of length mcap + ncap), or
+// P = 0 when the single-CTA kernel is used.  The stacked columns stay in
+// shared memory when the capacities allow; otherwise they live in the
+// state's global workspace, and the kernel still keeps them in shared
+// memory whenever the actual bond dimensions fit the allocation given here.
+struct SvdPlan {
+  int P = 0;
+  int threads = 0;
+  size_t smem = 0;
+  bool global = false;
+};
+
+template <typename S, typename R> static SvdPlan cluster_svd_plan(int mcap, int ncap) {
+  SvdPlan pl;
   // FP64 runs at 2 FMA/clk/SM on this part, so even small FP64 thetas gain
   // from spreading their columns over several SMs; FP32 ones only from 96.
-  if (ncap < (sizeof(S) == 8 ? 32 : 96)) return 0;
+  if (ncap < (sizeof(S) == 8 ? 32 : 96)) return pl;
   static int max16 = -1;
   static std::once_flag f;
   std::call_once(f, [] {
@@ -167,13 +178,25 @@ template <typename S, typename R> static int cluster_svd_size(int mcap, int ncap
     }
     max16 = n;
   });
+  const size_t lim = max_dyn_smem() - 2048;
   for (int P = ncap < 64 ? 4 : ((ncap >= 192 && max16 > 0) ? 16 : 8); P <= 16; P *= 2) {
     if (P == 16 && max16 <= 0) break;
     const int b = (ncap + 2 * P - 1) / (2 * P);
-    ClusterSvdSmem<S> L(b, mcap + ncap, 2 * P * b, 512);
-    if (L.total + 2048 <= max_dyn_smem() && 32 * b <= 512) return P;
+    ClusterSvdSmem<S> L(b, mcap + ncap, 2 * P * b, 32 * b);
+    if (L.total <= lim && 32 * b <= 512) {
+      pl.P = P;
+      pl.threads = 32 * b;
+      pl.smem = L.total;
+      return pl;
+    }
   }
-  return 0;
+  const int P = max16 > 0 ? 16 : 8;
+  const int b = (ncap + 2 * P - 1) / (2 * P);
+  pl.P = P;
+  pl.threads = 32 * std::min(b, 16);
+  pl.global = true;
+  pl.smem = std::min(lim, std::max(ClusterSvdSmem<S>(b, 0, 2 * P * b, pl.threads).total, (size_t)96 * 1024));
+  return pl;
 }
 
 template <typename R, typename S>
@@ -181,7 +204,8 @@ static void launch_two_qubit(mps_state* st, const DevGate* g, int q, cudaStream_
   const int cap_l = st->cap[q], cap_m = st->cap[q + 1], cap_r = st->cap[q + 2];
   const dim3 blk(kTile, kTile);
   const dim3 g1((cap_r + kTile - 1) / kTile, (cap_l + kTile - 1) / kTile);
-  const int P = cluster_svd_size<S, R>(2 * cap_l, 2 * cap_r);
+  const SvdPlan plan = cluster_svd_plan<S, R>(2 * cap_l, 2 * cap_r);
+  const int P = plan.P;
   {
     KernelScope k(st->ctx, MPS_K_THETA);
     theta_kernel<R, S><<<g1, blk, 0, s>>>(site_ptr<R>(st, q), site_ptr<R>(st, q + 1), g,
@@ -194,14 +218,13 @@ static void launch_two_qubit(mps_state* st, const DevGate* g, int q, cudaStream_
   p.max_sweeps = st->cfg.svd_max_sweeps > 0 ? st->cfg.svd_max_sweeps : 60;
   p.trunc_rel = st->cfg.trunc_rel;
   p.tol = st->cfg.svd_tol;
+  p.mixed = st->cfg.svd_fp64 == 2 ? 0 : 1;
   const dim3 g3((cap_m + kTile - 1) / kTile, (2 * cap_l + kTile - 1) / kTile);
   if (P) {
-    const int b = (2 * cap_r + 2 * P - 1) / (2 * P);
-    ClusterSvdSmem<S> L(b, 2 * cap_l + 2 * cap_r, 2 * P * b, 512);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(P);
-    cfg.blockDim = dim3(32 * b);  // one warp per column pair
-    cfg.dynamicSmemBytes = L.total;
+    cfg.blockDim = dim3(plan.threads);  // one warp per column pair
+    cfg.dynamicSmemBytes = plan.smem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -214,7 +237,8 @@ static void launch_two_qubit(mps_state* st, const DevGate* g, int q, cudaStream_
       KernelScope k(st->ctx, MPS_K_SVD);
       cudaLaunchKernelEx(&cfg, svd_cluster_kernel<S, R>, (const cplx<R>*)reinterpret_cast<cplx<R>*>(st->d_C),
                          (const double*)(st->d_lam + st->lam_off[q]), st->d_chi, q, p, site_ptr<R>(st, q + 1),
-                         st->d_lam + st->lam_off[q + 1], st->d_rep);
+                         st->d_lam + st->lam_off[q + 1], st->d_rep,
+                         plan.global ? reinterpret_cast<cplx<S>*>(st->d_A) : (cplx<S>*)nullptr, (unsigned)plan.smem);
     }
     {
       KernelScope k(st->ctx, MPS_K_G3);
@@ -487,6 +511,10 @@ mps_status mps_create(mps_ctx* ctx, int32_t n_qubits, const uint8_t* init_bits, 
     set_error("mps_create: unknown precision %d", cfg->precision);
     return MPS_EINVAL;
   }
+  if (cfg->svd_fp64 < 0 || cfg->svd_fp64 > 2) {
+    set_error("mps_create: svd_fp64 = %d is not 0, 1 or 2", cfg->svd_fp64);
+    return MPS_EINVAL;
+  }
   if (!(cfg->trunc_rel >= 0.0 && cfg->trunc_rel < 1.0)) {
     set_error("mps_create: trunc_rel = %g outside [0, 1)", cfg->trunc_rel);
     return MPS_EINVAL;
@@ -505,7 +533,7 @@ mps_status mps_create(mps_ctx* ctx, int32_t n_qubits, const uint8_t* init_bits, 
   st->site_off.resize(n);
   st->lam_off.resize(n + 1);
   size_t off = 0, loff = 0;
-  size_t max_mn = 1, max_nn = 1;
+  size_t max_mn = 1, max_nn = 1, max_stack = 1;
   for (int s = 0; s < n; ++s) {
     st->site_off[s] = off;
     off += (size_t)st->cap[s] * 2 * st->cap[s + 1];
@@ -517,6 +545,7 @@ mps_status mps_create(mps_ctx* ctx, int32_t n_qubits, const uint8_t* init_bits, 
   for (int q = 0; q + 1 < n; ++q) {
     const size_t m = 2 * (size_t)st->cap[q], nn = 2 * (size_t)st->cap[q + 2];
     max_mn = std::max(max_mn, m * nn);
+    max_stack = std::max(max_stack, cluster_svd_workspace(m, nn, st->svd64 ? 8 : 4));
     max_nn = std::max(max_nn, nn * nn);
   }
   st->total_elems = off;
@@ -535,7 +564,7 @@ mps_status mps_create(mps_ctx* ctx, int32_t n_qubits, const uint8_t* init_bits, 
   A((void**)&st->d_bits, n);
   A((void**)&st->d_rep, sizeof(DevReport));
   A(&st->d_C, max_mn * celem);
-  A(&st->d_A, max_mn * selem);
+  A(&st->d_A, std::max(max_mn, max_stack) * selem);  // theta copy, or the cluster SVD's stacked columns
   A(&st->d_V, max_nn * selem);
   if (rc != MPS_OK) {
     destroy_state(st);
@@ -589,6 +618,9 @@ mps_status mps_get_report(mps_state* st, mps_report* out) {
   out->max_sweeps_used = r.max_sweeps;
   out->two_qubit_gates = r.two_qubit_gates;
   out->svd_flops = r.svd_flops;
+  out->svd_sweeps_fp32 = r.sweeps_fp32;
+  out->svd_sweeps_fp64 = r.sweeps_fp64;
+  for (int i = 0; i < 4; ++i) out->svd_phase_cycles[i] = r.phase_cycles[i];
   return MPS_OK;
 }
 

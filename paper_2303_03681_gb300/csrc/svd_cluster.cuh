@@ -18,7 +18,20 @@
 // between its two blocks (and, in the first round, also the pairs inside
 // each block), then every block except the one at position 0 advances one
 // position.  Blocks move through distributed shared memory into ping-pong
-// buffers, so one cluster barrier per round orders the hand-over.
+// buffers, so one cluster barrier per round orders the hand-over.  When the
+// stacked columns do not fit the shared memory they stay in a global
+// workspace, and a round only renames the positions.
+//
+// FP64 accuracy at FP32 speed (complex64 states).  This part runs FP64 at
+// 2 FMA/clk/SM, so an all-FP64 Jacobi of a 100-column theta takes tens of
+// milliseconds.  The mixed form runs the sweeps in FP32 to FP32 convergence
+// (V32 accumulated as usual), re-orthonormalises V32 in FP64 with one
+// pairwise first-order step v_i <- v_i - 1/2 sum_j (v_j^H v_i) v_j (the
+// symmetric update V (I - E / 2), E = V^H V - I, which leaves ||E||^2),
+// rebuilds A = C~ V in FP64 from the theta, and finishes with FP64 sweeps,
+// which start near convergence and converge quadratically.  The singular
+// values, the truncation and B~_{q+1} then come from FP64 columns exactly as
+// in the all-FP64 form.
 #pragma once
 
 #include <cooperative_groups.h>
@@ -43,20 +56,6 @@ __device__ __forceinline__ void pos_owner(int pos, int P, int& rank, int& slot) 
 // Stacked-column elements a lane keeps in registers in the cross rounds
 // (columns up to 32 * kClusterRegs = 512 entries long).
 constexpr int kClusterRegs = 16;
-
-// Rotation of a column pair from its Gram entries (Algorithm 1 with the phase
-// of b_ij moved onto column j); returns false when the pair is left alone.
-template <typename S>
-__device__ __forceinline__ bool jacobi_rotation(S alpha, S beta, S gr, S gi, S tol, S floor, S tiny, S& c, cplx<S>& sph) {
-  const S mag = sqrt(gr * gr + gi * gi);
-  if (!(mag > tiny) || !(mag > tol * sqrt(alpha * beta)) || !(min(alpha, beta) > floor)) return false;
-  const S zeta = (beta - alpha) / (S(2) * mag);
-  const S t = (zeta >= S(0) ? S(1) : S(-1)) / (fabs(zeta) + sqrt(S(1) + zeta * zeta));
-  c = S(1) / sqrt(S(1) + t * t);
-  const S s = t * c;
-  sph = cmk<S>(s * gr / mag, s * gi / mag);  // s e^{i phi}
-  return true;
-}
 
 template <typename S>
 __device__ __forceinline__ void warp_sum4(S& a, S& b, S& c, S& d) {
@@ -128,6 +127,177 @@ __device__ __forceinline__ int jacobi_pair_reg(cplx<S> (&x)[kClusterRegs], cplx<
   return 1;
 }
 
+
+
+// Symmetric first-order orthonormalisation of the V parts (rows m .. len) of
+// two stacked columns: with e = v_i^H v_j, v_i -= conj(e)/2 v_j and
+// v_j -= e/2 v_i (from the old values).
+template <typename S>
+__device__ __forceinline__ void orth_pair(cplx<S>* vi, cplx<S>* vj, int m, int len, int lane) {
+  S gr = 0, gi = 0;
+  for (int r = m + lane; r < len; r += 32) {
+    const cplx<S> x = vi[r], y = vj[r];
+    gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+    gi = fma(x.x, y.y, fma(-x.y, y.x, gi));
+  }
+  gr = S(0.5) * warp_sum(gr);
+  gi = S(0.5) * warp_sum(gi);
+  for (int r = m + lane; r < len; r += 32) {
+    const cplx<S> x = vi[r], y = vj[r];
+    vi[r] = cmk<S>(x.x - fma(gr, y.x, gi * y.y), x.y - fma(gr, y.y, -gi * y.x));
+    vj[r] = cmk<S>(y.x - fma(gr, x.x, -gi * x.y), y.y - fma(gr, x.y, gi * x.x));
+  }
+}
+
+// Cluster-uniform sizes of one SVD.
+struct ClusterGeom {
+  int Pl, me;   // CTAs launched, this CTA's rank
+  int P, b;     // CTAs taking part, columns per block
+  int m, ncols, len, ncols_pad;
+  int nw, nt, wl, wp;
+  bool member;  // me < P
+};
+
+// Stacked columns of one precision: shared-memory ping-pong slots
+// [pp][slot][c][len], or (sm == nullptr) 2P global blocks [block][c][len]
+// that stay put while the round robin renames positions.
+template <typename T>
+struct ColStore {
+  cplx<T>* sm;
+  cplx<T>* gm;
+  int b, len, P, me;
+  __device__ cplx<T>* col(int pp, int slot, int c, int rnd) const {
+    if (sm) return sm + ((size_t)(pp * 2 + slot) * b + c) * len;
+    const int pos = slot == 0 ? me : 2 * P - 1 - me;
+    const int M = 2 * P - 1;
+    const int blk = pos == 0 ? 0 : 1 + ((pos - 1 - rnd) % M + M) % M;
+    return gm + ((size_t)blk * b + c) * len;
+  }
+};
+
+// Sweeps of the circle-method round robin.  kOp 0: Jacobi rotations until a
+// sweep rotates no pair (or max_sweeps); kOp 1: max_sweeps orthonormalisation
+// sweeps.  Every CTA of the cluster calls it (non-members only keep the
+// cluster barriers in step).  Returns the sweeps run.
+template <typename T, int kOp>
+__device__ int cluster_sweeps(const ClusterGeom& g, const ColStore<T>& cs, int& cur, int max_sweeps, T tol, T floor,
+                              T tiny, bool& converged, const cg::cluster_group& cluster, int* s_flag_in,
+                              int* s_any) {
+  using C = cplx<T>;
+  // In the cross rounds, when every warp has one top-slot column, warp w
+  // keeps it in registers for the b rotations it takes part in; only the
+  // bottom-slot columns are re-read, so one barrier per sub-round orders
+  // their hand-off.
+  const bool cache_x = kOp == 0 && g.len <= 32 * kClusterRegs && g.b <= g.nw;
+  const bool active = g.member && g.wp < g.b;
+  int sweep = 0;
+  converged = false;
+  for (; sweep < max_sweeps; ++sweep) {
+    int rotated = 0;
+    for (int rnd = 0; rnd < 2 * g.P - 1; ++rnd) {
+      if (!g.member) {
+        // not taking part: only the cluster barrier below
+      } else if (rnd == 0) {
+        // every pair among the CTA's 2b columns: round robin over 2b players
+        const int mod = 2 * g.b - 1;
+        for (int sr = 0; sr < 2 * g.b - 1; ++sr) {
+          for (int pw = g.wp; pw < g.b; pw += g.nw) {
+            int a0, a1;
+            if (pw == 0) {
+              a0 = mod;
+              a1 = sr;
+            } else {
+              a0 = (sr + pw) % mod;
+              a1 = (sr - pw + mod) % mod;
+            }
+            C* x = cs.col(cur, a0 / g.b, a0 % g.b, rnd);
+            C* y = cs.col(cur, a1 / g.b, a1 % g.b, rnd);
+            if (kOp == 0)
+              rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tol, floor, tiny);
+            else
+              orth_pair<T>(x, y, g.m, g.len, g.wl);
+          }
+          __syncthreads();
+        }
+      } else {
+        C xr[kClusterRegs];
+        C* xcol = cs.col(cur, 0, active ? g.wp : 0, rnd);
+        if (active && cache_x) {
+#pragma unroll
+          for (int i = 0; i < kClusterRegs; ++i) {
+            const int r = g.wl + 32 * i;
+            xr[i] = r < g.len ? xcol[r] : cmk<T>(0, 0);
+          }
+        }
+        for (int sr = 0; sr < g.b; ++sr) {
+          if (cache_x) {
+            if (active)
+              rotated |= jacobi_pair_reg<T>(xr, cs.col(cur, 1, (g.wp + sr) % g.b, rnd), g.m, g.len, g.wl, tol,
+                                            floor, tiny);
+          } else {
+            for (int pw = g.wp; pw < g.b; pw += g.nw) {
+              C* x = cs.col(cur, 0, pw, rnd);
+              C* y = cs.col(cur, 1, (pw + sr) % g.b, rnd);
+              if (kOp == 0)
+                rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tol, floor, tiny);
+              else
+                orth_pair<T>(x, y, g.m, g.len, g.wl);
+            }
+          }
+          __syncthreads();
+        }
+        if (active && cache_x) {
+#pragma unroll
+          for (int i = 0; i < kClusterRegs; ++i) {
+            const int r = g.wl + 32 * i;
+            if (r < g.len) xcol[r] = xr[i];
+          }
+        }
+        __syncthreads();
+      }
+      if (g.P == 1) continue;  // a single CTA keeps its blocks (and needs no cluster barrier)
+      if (cs.sm) {
+        // hand the blocks on: position pos -> pos + 1 (pos >= 1), 2P-1 -> 1
+        const int nxt = cur ^ 1;
+        const size_t units = (size_t)g.b * g.len * sizeof(C) / sizeof(uint4);
+        for (int slot = 0; slot < 2 && g.member; ++slot) {
+          const int pos = slot == 0 ? g.me : 2 * g.P - 1 - g.me;
+          const int npos = pos == 0 ? 0 : (pos == 2 * g.P - 1 ? 1 : pos + 1);
+          int drank, dslot;
+          pos_owner(npos, g.P, drank, dslot);
+          const uint4* src = reinterpret_cast<const uint4*>(cs.col(cur, slot, 0, 0));
+          uint4* dst = reinterpret_cast<uint4*>(cluster.map_shared_rank(cs.col(nxt, dslot, 0, 0), drank));
+          for (size_t t = threadIdx.x; t < units; t += g.nt) dst[t] = src[t];
+        }
+        cluster.sync();
+        cur = nxt;
+      } else {
+        cluster.sync();  // global columns: this round's writes before the next round's reads
+      }
+    }
+    if (kOp == 1) continue;
+    // ---- convergence: every CTA tells every CTA whether it rotated
+    if (threadIdx.x == 0) *s_any = 0;
+    __syncthreads();
+    if (rotated) *s_any = 1;
+    __syncthreads();
+    if (threadIdx.x < g.Pl) {
+      int* dst = cluster.map_shared_rank(s_flag_in, (int)threadIdx.x);
+      dst[g.me] = *s_any;
+    }
+    cluster.sync();
+    int any = 0;
+    for (int r2 = 0; r2 < g.Pl; ++r2) any |= s_flag_in[r2];
+    cluster.sync();  // all reads done before the next sweep's writes
+    if (!any) {
+      converged = true;
+      ++sweep;
+      break;
+    }
+  }
+  return sweep;
+}
+
 template <typename S>
 struct ClusterSvdSmem {
   // layout of the dynamic shared memory (offsets in bytes); len = m + n
@@ -144,215 +314,224 @@ struct ClusterSvdSmem {
   }
 };
 
+// Elements of cplx<S> the global workspace needs for a theta of capacity
+// mcap x ncap: the stacked columns (at most 2 P - 1 padding columns, P <= 16)
+// in S, plus an FP32 copy for the mixed form.
+__host__ __device__ inline size_t cluster_svd_workspace(size_t mcap, size_t ncap, size_t s_bytes) {
+  const size_t e = (ncap + 32) * (mcap + ncap);
+  return s_bytes == 8 ? e + (e + 1) / 2 : e;
+}
+
 template <typename S, typename R>
 __global__ void __launch_bounds__(512, 1)
     svd_cluster_kernel(const cplx<R>* __restrict__ Cm, const double* __restrict__ lam_l, int* __restrict__ chi, int q,
                        SvdParams p, cplx<R>* __restrict__ Bnext, double* __restrict__ lam_next,
-                       DevReport* __restrict__ rep) {
+                       DevReport* __restrict__ rep, cplx<S>* __restrict__ gbuf, unsigned smem_bytes) {
   using C = cplx<S>;
   cg::cluster_group cluster = cg::this_cluster();
-  const int P = (int)cluster.num_blocks();
-  const int me = (int)cluster.block_rank();
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_flag_in[16];
   __shared__ double s_fro[16];
   __shared__ int s_k;
   __shared__ double s_nrm;
+  __shared__ int s_any;
 
+  const long long t_start = clock64();
+  long long t_load = 0, t_lo = 0, t_fix = 0;
+  ClusterGeom g;
+  g.Pl = (int)cluster.num_blocks();  // CTAs launched (sized for the bond capacities)
+  g.me = (int)cluster.block_rank();
   const int chi_l = chi[q], chi_r = chi[q + 2];
-  const int m = 2 * chi_l;      // rows of A
-  const int ncols = 2 * chi_r;  // columns of A = rows of V
-  const int len = m + ncols;    // stacked column [A; V]
-  const int b = (ncols + 2 * P - 1) / (2 * P);
-  const int ncols_pad = 2 * P * b;
-  const int nt = blockDim.x;
-  const ClusterSvdSmem<S> L(b, len, ncols_pad, nt);
-  C* bufs = reinterpret_cast<C*>(smem + L.buf);
+  g.m = 2 * chi_l;      // rows of A
+  g.ncols = 2 * chi_r;  // columns of A = rows of V
+  g.len = g.m + g.ncols;
+  g.nw = (int)(blockDim.x >> 5);
+  g.nt = blockDim.x;
+  g.wl = threadIdx.x & 31;
+  g.wp = threadIdx.x >> 5;
+  const bool mixed = sizeof(S) == 8 && sizeof(R) == 4 && p.mixed;
+  // CTAs that take part, from the actual bond dimensions: complex64 pair
+  // steps are latency-bound, so as few CTAs as the warps allow (fewer rounds
+  // and cluster barriers); FP64 ones are bound by the FP64 units, so one pair
+  // per warp on as many CTAs as there are.  The others (rank >= P) only keep
+  // the cluster barriers in step.
+  const int per = sizeof(S) == 8 ? 1 : g.nw;
+  g.P = min(g.Pl, max(1, (g.ncols + 2 * per - 1) / (2 * per)));
+  g.member = g.me < g.P;
+  g.b = (g.ncols + 2 * g.P - 1) / (2 * g.P);  // a warp takes pairs w, w + nw, ...
+  g.ncols_pad = 2 * g.P * g.b;
+  const int m = g.m, ncols = g.ncols, len = g.len, b = g.b, P = g.P, me = g.me, nt = g.nt;
+
+  // Shared memory when the stacked columns fit the launch's allocation, else the global workspace.
+  const bool in_smem = gbuf == nullptr || ClusterSvdSmem<S>(b, len, g.ncols_pad, nt).total <= smem_bytes;
+  const ClusterSvdSmem<S> L(b, in_smem ? len : 0, g.ncols_pad, nt);
   double* sig = reinterpret_cast<double*>(smem + L.sig);
   int* rnk = reinterpret_cast<int*>(smem + L.rank);
-  const size_t slot_elems = (size_t)b * len;
-  auto col_ptr = [&](int pp, int slot, int c) -> C* { return bufs + ((size_t)(pp * 2 + slot) * b + c) * len; };
+  const ColStore<S> cs{in_smem ? reinterpret_cast<C*>(smem + L.buf) : nullptr, gbuf, b, len, P, me};
+  // FP32 columns of the mixed form: in shared memory both FP32 ping-pong
+  // buffers fit in the first S ping-pong buffer; in global memory they follow
+  // the S blocks.
+  const ColStore<float> cs32{in_smem ? reinterpret_cast<cplx<float>*>(smem + L.buf) : nullptr,
+                             in_smem ? nullptr : reinterpret_cast<cplx<float>*>(gbuf + (size_t)g.ncols_pad * len), b,
+                             len, P, me};
 
   // ---- load: position pos holds the initial block pos (columns pos*b ..)
-  for (int slot = 0; slot < 2; ++slot) {
+  for (int slot = 0; slot < 2 && g.member; ++slot) {
     const int pos = slot == 0 ? me : 2 * P - 1 - me;
-    for (size_t t = threadIdx.x; t < slot_elems; t += nt) {
+    for (size_t t = threadIdx.x; t < (size_t)b * len; t += nt) {
       const int c = (int)(t / len), r = (int)(t % len);
       const int col = pos * b + c;
-      C v = cmk<S>(0, 0);
+      double vr = 0.0, vi = 0.0;
       if (col < ncols) {
         if (r < m) {
           const cplx<R> x = Cm[(size_t)r * ncols + col];
-          const S w = S(lam_l[r >> 1]);
-          v = cmk<S>(w * S(x.x), w * S(x.y));
+          const double w = lam_l[r >> 1];
+          vr = w * double(x.x);
+          vi = w * double(x.y);
         } else if (r - m == col) {
-          v = cmk<S>(1, 0);
+          vr = 1.0;
         }
       }
-      col_ptr(0, slot, c)[r] = v;
+      if (mixed)
+        cs32.col(0, slot, c, 0)[r] = cmk<float>(float(vr), float(vi));
+      else
+        cs.col(0, slot, c, 0)[r] = cmk<S>(S(vr), S(vi));
     }
   }
-  __syncthreads();
-  // ||A||_F^2: each CTA's share goes to every CTA, summed in rank order
+  // ||A||_F^2 from the theta: each CTA's share goes to every CTA, summed in rank order
   double part = 0.0;
-  for (size_t t = threadIdx.x; t < 2 * slot_elems; t += nt) {
-    if ((int)(t % len) >= m) continue;
-    const C v = bufs[t];
-    part += double(v.x) * v.x + double(v.y) * v.y;
+  for (size_t t = threadIdx.x; g.member && t < (size_t)2 * b * m; t += nt) {
+    const int c = (int)(t / m), r = (int)(t % m);
+    const int pos = c < b ? me : 2 * P - 1 - me;
+    const int col = pos * b + c % b;
+    if (col >= ncols) continue;
+    const cplx<R> x = Cm[(size_t)r * ncols + col];
+    const double w = lam_l[r >> 1];
+    part += w * w * (double(x.x) * x.x + double(x.y) * x.y);
   }
   part = warp_sum(part);
   if (threadIdx.x == 0) s_nrm = 0.0;
   __syncthreads();
   if ((threadIdx.x & 31) == 0) atomicAdd(&s_nrm, part);
   __syncthreads();
-  if (threadIdx.x < P) *cluster.map_shared_rank(&s_fro[me], (int)threadIdx.x) = s_nrm;
+  if (threadIdx.x < g.Pl) *cluster.map_shared_rank(&s_fro[me], (int)threadIdx.x) = s_nrm;
   cluster.sync();
   double fro2 = 0.0;
-  for (int r2 = 0; r2 < P; ++r2) fro2 += s_fro[r2];
+  for (int r2 = 0; r2 < g.Pl; ++r2) fro2 += s_fro[r2];
 
   // Stopping rule and rounding floor: rotate while |b_ij| > tol sqrt(b_ii b_jj)
   // with tol = 4 sqrt(max(m, n)) u (a few times the rounding error of a dot
   // product); columns with squared norm below (4 u ||A||_F)^2 are rounding
   // noise and left alone.
+  const double tol_scale = 4.0 * sqrt(double(max(m, ncols)));
+  int cur = 0, used = 0, used32 = 0;
+  bool converged = false;
+  t_load = clock64();
+  t_lo = t_fix = t_load;
+  if (mixed) {
+    const float u32 = 5.9604645e-08f;
+    int cur32 = 0;
+    bool conv32 = false;
+    used32 = cluster_sweeps<float, 0>(g, cs32, cur32, p.max_sweeps, float(tol_scale) * u32,
+                                      float(16.0 * double(u32) * double(u32) * fro2), 1e-35f, conv32, cluster,
+                                      s_flag_in, &s_any);
+    used = used32;
+    t_lo = clock64();
+    // FP64 columns: V promoted (A follows from the theta below)
+    cur = in_smem ? 1 : 0;
+    for (int slot = 0; slot < 2 && g.member; ++slot)
+      for (size_t t = threadIdx.x; t < (size_t)b * ncols; t += nt) {
+        const int c = (int)(t / ncols), r = m + (int)(t % ncols);
+        const cplx<float> v = cs32.col(cur32, slot, c, 0)[r];
+        cs.col(cur, slot, c, 0)[r] = cmk<S>(S(v.x), S(v.y));
+      }
+    // every CTA has read its FP32 columns before the first hand-over may
+    // overwrite them (in shared memory they share a buffer with FP64 ones)
+    cluster.sync();
+    bool dummy;
+    cluster_sweeps<S, 1>(g, cs, cur, 1, S(0), S(0), S(0), dummy, cluster, s_flag_in, &s_any);
+    // the diagonal of the first-order step: |v|^2 -> 1
+    for (int c = g.wp; g.member && c < 2 * b; c += g.nw) {
+      C* v = cs.col(cur, c / b, c % b, 0);
+      S n2 = 0;
+      for (int r = m + g.wl; r < len; r += 32) n2 = fma(v[r].x, v[r].x, fma(v[r].y, v[r].y, n2));
+      n2 = warp_sum(n2);
+      const S f = S(1.5) - S(0.5) * n2;
+      if (n2 > S(0))
+        for (int r = m + g.wl; r < len; r += 32) v[r] = cmk<S>(f * v[r].x, f * v[r].y);
+    }
+    __syncthreads();
+    // A = C~ V in FP64 for this CTA's columns
+    for (size_t t = threadIdx.x; g.member && t < (size_t)2 * b * m; t += nt) {
+      const int c = (int)(t / m), r = (int)(t % m);
+      C* x = cs.col(cur, c / b, c % b, 0);
+      const cplx<R>* crow = Cm + (size_t)r * ncols;
+      S ar = 0, ai = 0;
+      for (int k = 0; k < ncols; ++k) {
+        const cplx<R> cv = crow[k];
+        const C v = x[m + k];
+        ar = fma(S(cv.x), v.x, fma(-S(cv.y), v.y, ar));
+        ai = fma(S(cv.x), v.y, fma(S(cv.y), v.x, ai));
+      }
+      const S w = S(lam_l[r >> 1]);
+      x[r] = cmk<S>(w * ar, w * ai);
+    }
+    __syncthreads();
+    t_fix = clock64();
+  }
   const S eps_u = sizeof(S) == 8 ? S(1.1102230246251565e-16) : S(5.9604645e-08f);
-  const S tol = p.tol > 0 ? S(p.tol) : S(4.0 * sqrt(double(max(m, ncols)))) * eps_u;
+  const S tol = p.tol > 0 ? S(p.tol) : S(tol_scale) * eps_u;
   const S floor = S(16.0 * double(eps_u) * double(eps_u) * fro2);
   const S tiny = sizeof(S) == 8 ? S(1e-290) : S(1e-35f);
-  // One warp per column pair (warps past b idle in the pair loops).  In the
-  // cross rounds warp w keeps its top-slot column in registers for the b
-  // rotations it takes part in; only the bottom-slot columns go through
-  // shared memory, so one barrier per sub-round orders their hand-off.
-  const int wl = threadIdx.x & 31, wp = threadIdx.x >> 5;
-  const bool active = wp < b;
-  const bool cache_x = len <= 32 * kClusterRegs;
-
-  int sweep = 0, cur = 0;
-  bool converged = false;
-  for (; sweep < p.max_sweeps; ++sweep) {
-    int rotated = 0;
-    for (int round = 0; round < 2 * P - 1; ++round) {
-      if (round == 0) {
-        // every pair among the CTA's 2b columns: round robin over 2b players
-        const int mod = 2 * b - 1;
-        for (int sr = 0; sr < 2 * b - 1; ++sr) {
-          if (active) {
-            int a0, a1;
-            if (wp == 0) {
-              a0 = mod;
-              a1 = sr;
-            } else {
-              a0 = (sr + wp) % mod;
-              a1 = (sr - wp + mod) % mod;
-            }
-            rotated |= jacobi_pair_smem<S>(col_ptr(cur, a0 / b, a0 % b), col_ptr(cur, a1 / b, a1 % b), m, len, wl,
-                                           tol, floor, tiny);
-          }
-          __syncthreads();
-        }
-      } else {
-        C xr[kClusterRegs];
-        C* xcol = col_ptr(cur, 0, active ? wp : 0);
-        if (active && cache_x) {
-#pragma unroll
-          for (int i = 0; i < kClusterRegs; ++i) {
-            const int r = wl + 32 * i;
-            xr[i] = r < len ? xcol[r] : cmk<S>(0, 0);
-          }
-        }
-        for (int sr = 0; sr < b; ++sr) {
-          if (active) {
-            C* aj = col_ptr(cur, 1, (wp + sr) % b);
-            rotated |= cache_x ? jacobi_pair_reg<S>(xr, aj, m, len, wl, tol, floor, tiny)
-                               : jacobi_pair_smem<S>(xcol, aj, m, len, wl, tol, floor, tiny);
-          }
-          __syncthreads();
-        }
-        if (active && cache_x) {
-#pragma unroll
-          for (int i = 0; i < kClusterRegs; ++i) {
-            const int r = wl + 32 * i;
-            if (r < len) xcol[r] = xr[i];
-          }
-        }
-        __syncthreads();
-      }
-      // ---- hand the blocks on: position pos -> pos + 1 (pos >= 1), 2P-1 -> 1
-      const int nxt = cur ^ 1;
-      const size_t units = slot_elems * sizeof(C) / sizeof(uint4);
-      for (int slot = 0; slot < 2; ++slot) {
-        const int pos = slot == 0 ? me : 2 * P - 1 - me;
-        int npos = pos == 0 ? 0 : (pos == 2 * P - 1 ? 1 : pos + 1);
-        int drank, dslot;
-        pos_owner(npos, P, drank, dslot);
-        const uint4* src = reinterpret_cast<const uint4*>(col_ptr(cur, slot, 0));
-        uint4* dst = reinterpret_cast<uint4*>(cluster.map_shared_rank(col_ptr(nxt, dslot, 0), drank));
-        for (size_t t = threadIdx.x; t < units; t += nt) dst[t] = src[t];
-      }
-      cluster.sync();
-      cur = nxt;
-    }
-    // ---- convergence: every CTA tells every CTA whether it rotated
-    __shared__ int s_any;
-    if (threadIdx.x == 0) s_any = 0;
-    __syncthreads();
-    if (rotated) s_any = 1;
-    __syncthreads();
-    if (threadIdx.x < P) {
-      int* dst = cluster.map_shared_rank(s_flag_in, (int)threadIdx.x);
-      dst[me] = s_any;
-    }
-    cluster.sync();
-    int any = 0;
-    for (int r2 = 0; r2 < P; ++r2) any |= s_flag_in[r2];
-    cluster.sync();  // all reads done before the next sweep's writes
-    if (!any) {
-      converged = true;
-      ++sweep;
-      break;
-    }
-  }
+  used += cluster_sweeps<S, 0>(g, cs, cur, p.max_sweeps, tol, floor, tiny, converged, cluster, s_flag_in, &s_any);
+  const int sweep = used;
 
   // ---- singular values: norms of the A parts, shared with every CTA
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nt >> 5;
-  for (int c = warp; c < 2 * b; c += nw) {
-    const C* a = col_ptr(cur, c / b, c % b);
+  const int lane = g.wl, warp = g.wp;
+  const int ncols_pad = g.ncols_pad;
+  for (int c = warp; g.member && c < 2 * b; c += g.nw) {
+    const C* a = cs.col(cur, c / b, c % b, 0);
     double acc = 0.0;
     for (int r = lane; r < m; r += 32) acc += double(a[r].x) * a[r].x + double(a[r].y) * a[r].y;
     acc = warp_sum(acc);
     if (lane == 0) {
       const double sv = sqrt(acc);
-      const int g = me * 2 * b + c;
-      for (int r2 = 0; r2 < P; ++r2) *cluster.map_shared_rank(sig + g, r2) = sv;
+      const int gc = me * 2 * b + c;
+      for (int r2 = 0; r2 < P; ++r2) *cluster.map_shared_rank(sig + gc, r2) = sv;
     }
   }
   cluster.sync();
+  if (!g.member) {
+    cluster.sync();  // pairs with the final barrier of the members
+    return;
+  }
   // ranks (descending, ties by index), the same in every CTA
-  for (int g = threadIdx.x; g < ncols_pad; g += nt) {
-    const double sg = sig[g];
+  for (int gc = threadIdx.x; gc < ncols_pad; gc += nt) {
+    const double sg = sig[gc];
     int rk = 0;
     for (int h = 0; h < ncols_pad; ++h) {
       const double sh = sig[h];
-      rk += (sh > sg) || (sh == sg && h < g);
+      rk += (sh > sg) || (sh == sg && h < gc);
     }
-    rnk[g] = rk;
+    rnk[gc] = rk;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
     double total = 0.0, smax = 0.0;
-    for (int g = 0; g < ncols_pad; ++g) {
-      total += sig[g] * sig[g];
-      smax = fmax(smax, sig[g]);
+    for (int gc = 0; gc < ncols_pad; ++gc) {
+      total += sig[gc] * sig[gc];
+      smax = fmax(smax, sig[gc]);
     }
     int cnt = 0;
-    for (int g = 0; g < ncols_pad; ++g)
-      if (p.trunc_rel > 0.0 ? (sig[g] > p.trunc_rel * smax) : (sig[g] > 0.0)) ++cnt;
+    for (int gc = 0; gc < ncols_pad; ++gc)
+      if (p.trunc_rel > 0.0 ? (sig[gc] > p.trunc_rel * smax) : (sig[gc] > 0.0)) ++cnt;
     int k = min(cnt, min(p.chi_max, min(m, ncols)));
     if (k < 1) k = 1;
     double kept = 0.0, smin = 0.0, s_next = 0.0;
-    for (int g = 0; g < ncols_pad; ++g) {
-      if (rnk[g] < k) kept += sig[g] * sig[g];
-      if (rnk[g] == k - 1) smin = sig[g];
-      if (rnk[g] == k) s_next = sig[g];
+    for (int gc = 0; gc < ncols_pad; ++gc) {
+      if (rnk[gc] < k) kept += sig[gc] * sig[gc];
+      if (rnk[gc] == k - 1) smin = sig[gc];
+      if (rnk[gc] == k) s_next = sig[gc];
     }
     double nrm = sqrt(kept);
     if (!(nrm > 0.0)) nrm = 1.0;
@@ -365,13 +544,20 @@ __global__ void __launch_bounds__(512, 1)
       if (k < ncols && k == p.chi_max && s_next > 0.0 && fabs(smin - s_next) <= 1e-10 * smin)
         rep->degenerate_cuts += 1;
       if (!converged) rep->not_converged += 1;
-      const int used = converged ? sweep : p.max_sweeps + 1;
-      if (used > rep->max_sweeps) rep->max_sweeps = used;
+      const int used_cap = converged ? sweep : p.max_sweeps + 1;
+      if (used_cap > rep->max_sweeps) rep->max_sweeps = used_cap;
       rep->two_qubit_gates += 1;
       // per sweep and column pair: three dot products over m rows (16 m flops)
       // and one rotation of the stacked columns (12 (m + n) flops)
-      rep->svd_flops += (double)min(used, p.max_sweeps) * 0.5 * ncols * (ncols - 1) * (16.0 * m + 12.0 * len);
+      rep->svd_flops += (double)sweep * 0.5 * ncols * (ncols - 1) * (16.0 * m + 12.0 * len);
       rep->inv_norm = 1.0 / nrm;
+      rep->sweeps_fp32 += used32;
+      (sizeof(S) == 8 ? rep->sweeps_fp64 : rep->sweeps_fp32) += sweep - used32;
+      const long long t_end = clock64();
+      rep->phase_cycles[0] += double(t_load - t_start);
+      rep->phase_cycles[1] += double(t_lo - t_load);
+      rep->phase_cycles[2] += double(t_fix - t_lo);
+      rep->phase_cycles[3] += double(t_end - t_fix);
       chi[q + 1] = k;
     }
   }
@@ -379,14 +565,14 @@ __global__ void __launch_bounds__(512, 1)
   const int k = s_k;
   const double inv = 1.0 / s_nrm;
   if (me == 0)
-    for (int g = threadIdx.x; g < ncols_pad; g += nt)
-      if (rnk[g] < k) lam_next[rnk[g]] = sig[g] * inv;
-  // B~_{q+1}[a, :] = conj(V[:, g]) for the column g of rank a < k
-  for (int c = warp; c < 2 * b; c += nw) {
-    const int g = me * 2 * b + c;
-    const int a = rnk[g];
+    for (int gc = threadIdx.x; gc < ncols_pad; gc += nt)
+      if (rnk[gc] < k) lam_next[rnk[gc]] = sig[gc] * inv;
+  // B~_{q+1}[a, :] = conj(V[:, gc]) for the column gc of rank a < k
+  for (int c = warp; c < 2 * b; c += g.nw) {
+    const int gc = me * 2 * b + c;
+    const int a = rnk[gc];
     if (a >= k) continue;
-    const C* v = col_ptr(cur, c / b, c % b) + m;
+    const C* v = cs.col(cur, c / b, c % b, 0) + m;
     for (int r = lane; r < ncols; r += 32) Bnext[(size_t)a * ncols + r] = ccast<cplx<R>>(cconj(v[r]));
   }
   cluster.sync();  // no CTA leaves while its shared memory may still be read

@@ -1,17 +1,18 @@
 // Tensor-core complex GEMM for sm_103a (tcgen05, accumulator in tensor
 // memory) with FP32 accuracy from TF32 products: every FP32 operand value x is
-// split into x_hi = tf32(x) and x_lo = x - x_hi, and each real product is
-// A_hi B_hi + A_hi B_lo + A_lo B_hi (the dropped A_lo B_lo is below FP32
-// rounding).
+// split into x_hi = tf32(x) and x_lo = tf32(x - x_hi), both rounded to
+// nearest, so x = x_hi + x_lo to about 2^-22 |x|; each real product is the sum
+// of the four TF32 products A_hi B_hi + A_hi B_lo + A_lo B_hi + A_lo B_lo
+// (each exact in the FP32 accumulator's precision).
 //
 // One CTA of 128 threads (one warpgroup) computes a 128 x 128 real tile.  Per
 // 32-wide real K chunk the threads stage A and B^T, split into hi and lo, in
 // shared memory in the canonical K-major 128-byte-swizzled layout (8-row
 // atoms of 1024 bytes; the 16-byte chunk c of row r sits at chunk c ^ (r mod
-// 8)); one thread issues the 4 x 3 tcgen05.mma (M 128, N 128, K 8) and
+// 8)); one thread issues the 4 x 4 tcgen05.mma (M 128, N 128, K 8) and
 // commits them to an mbarrier that every thread waits on with a bounded spin.
-// The epilogue reads the accumulator with tcgen05.ld (warp w owns rows
-// 32w..32w+31).  A wait that runs out sets *err; the accumulator is released
+// After each chunk the threads read its product with tcgen05.ld (warp w owns
+// rows 32w..32w+31) and add it to FP32 sums in registers.  A wait that runs out sets *err; the accumulator is released
 // in every case.
 #pragma once
 
@@ -91,6 +92,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
+// 32 lanes x 16 consecutive 32-bit columns of tensor memory into v (this warp's lane quarter)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -147,6 +158,9 @@ __global__ void __launch_bounds__(kThreads, 1) cgemm_kernel(Prob prob, int tiles
 
   uint32_t phase = 0;
   bool ok = true;
+  float acc[kBN];
+#pragma unroll
+  for (int j = 0; j < kBN; ++j) acc[j] = 0.f;
   const int nk = (K + kKC - 1) / kKC;
   for (int kc = 0; kc < nk && ok; ++kc) {
     const int k0 = kc * kKC;
@@ -159,9 +173,9 @@ __global__ void __launch_bounds__(kThreads, 1) cgemm_kernel(Prob prob, int tiles
       const float rh = tf32_hi(v.x), ih = tf32_hi(v.y);
       const uint32_t o0 = swz_offset(r, 2 * kk), o1 = swz_offset(r, 2 * kk + 1);
       *reinterpret_cast<float*>(tA_hi + o0) = rh;
-      *reinterpret_cast<float*>(tA_lo + o0) = v.x - rh;
+      *reinterpret_cast<float*>(tA_lo + o0) = tf32_hi(v.x - rh);
       *reinterpret_cast<float*>(tA_hi + o1) = ih;
-      *reinterpret_cast<float*>(tA_lo + o1) = v.y - ih;
+      *reinterpret_cast<float*>(tA_lo + o1) = tf32_hi(v.y - ih);
     }
     // B^T: 64 complex columns n x 16 complex k -> 2 x 2 real blocks
     for (int e = tid; e < (kBN / 2) * kKC; e += kThreads) {
@@ -170,7 +184,7 @@ __global__ void __launch_bounds__(kThreads, 1) cgemm_kernel(Prob prob, int tiles
       float2 v = make_float2(0.f, 0.f);
       if (gn < N && gk < K) v = prob.b(z, gk, gn);
       const float rh = tf32_hi(v.x), ih = tf32_hi(v.y), nih = -ih;
-      const float rl = v.x - rh, il = v.y - ih;
+      const float rl = tf32_hi(v.x - rh), il = tf32_hi(v.y - ih);
       const uint32_t o00 = swz_offset(2 * nn, 2 * kk), o01 = swz_offset(2 * nn, 2 * kk + 1);
       const uint32_t o10 = swz_offset(2 * nn + 1, 2 * kk), o11 = swz_offset(2 * nn + 1, 2 * kk + 1);
       *reinterpret_cast<float*>(tB_hi + o00) = rh;
@@ -191,9 +205,10 @@ __global__ void __launch_bounds__(kThreads, 1) cgemm_kernel(Prob prob, int tiles
 #pragma unroll
       for (int ks = 0; ks < kBK / 8; ++ks) {
         const uint64_t adv = (uint64_t)((ks * 32) >> 4);  // 8 tf32 = 32 bytes along K
-        mma_tf32(tmem, dAh + adv, dBh + adv, idesc, (kc > 0 || ks > 0) ? 1u : 0u);
+        mma_tf32(tmem, dAh + adv, dBh + adv, idesc, ks > 0 ? 1u : 0u);
         mma_tf32(tmem, dAh + adv, dBl + adv, idesc, 1u);
         mma_tf32(tmem, dAl + adv, dBh + adv, idesc, 1u);
+        mma_tf32(tmem, dAl + adv, dBl + adv, idesc, 1u);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
           smem_u32(&mbar)));
@@ -202,26 +217,30 @@ __global__ void __launch_bounds__(kThreads, 1) cgemm_kernel(Prob prob, int tiles
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
-    if (s_fail) ok = false;
+    if (s_fail) {
+      ok = false;
+    } else {
+      // the chunk's partial product joins the FP32 sum in registers (rounded
+      // to nearest), which keeps the tensor cores' own accumulation chains
+      // to one chunk of 32 real K
+#pragma unroll
+      for (int c0 = 0; c0 < kBN; c0 += 16) {
+        uint32_t v[16];
+        tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(v[j]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");  // loads done before the next chunk's MMAs
+    }
   }
 
   if (ok) {
-    const int row = m0 + warp * 32 + lane;  // warp w reads accumulator rows 32w .. 32w+31
-    for (int c0 = 0; c0 < kBN; c0 += 16) {
-      uint32_t v[16];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (row < M) {
+    const int row = m0 + warp * 32 + lane;  // warp w holds accumulator rows 32w .. 32w+31
+    if (row < M) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int col = n0 + c0 / 2 + j;
-          if (col < N) prob.store(z, row, col, make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1])));
-        }
+      for (int j = 0; j < kBN / 2; ++j) {
+        const int col = n0 + j;
+        if (col < N) prob.store(z, row, col, make_float2(acc[2 * j], acc[2 * j + 1]));
       }
     }
   } else if (tid == 0) {

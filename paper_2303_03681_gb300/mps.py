@@ -44,10 +44,12 @@ class Report(ctypes.Structure):
     _fields_ = [("discarded_weight", ctypes.c_double), ("min_kept_sv", ctypes.c_double),
                 ("max_chi", ctypes.c_int32), ("degenerate_cuts", ctypes.c_int32),
                 ("svd_not_converged", ctypes.c_int32), ("max_sweeps_used", ctypes.c_int32),
-                ("two_qubit_gates", ctypes.c_int64), ("svd_flops", ctypes.c_double)]
+                ("two_qubit_gates", ctypes.c_int64), ("svd_flops", ctypes.c_double),
+                ("svd_sweeps_fp32", ctypes.c_int64), ("svd_sweeps_fp64", ctypes.c_int64),
+                ("svd_phase_cycles", ctypes.c_double * 4)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: (list(getattr(self, k)) if k == "svd_phase_cycles" else getattr(self, k)) for k, _ in self._fields_}
 
 
 class VqeRequest(ctypes.Structure):
@@ -321,7 +323,7 @@ class State(_Child):
                  tensor_cores: bool = False):
         self._adopt(ctx)
         self.n = int(n_qubits)
-        self.cfg = Config(int(chi_max), PRECISIONS[precision], float(trunc_rel), 1 if svd_fp64 else 0,
+        self.cfg = Config(int(chi_max), PRECISIONS[precision], float(trunc_rel), int(svd_fp64),
                           int(svd_max_sweeps), float(svd_tol), 1 if tensor_cores else 0)
         bits = None if init_bits is None else np.ascontiguousarray(init_bits, dtype=np.uint8)
         h = ctypes.c_void_p()
@@ -475,7 +477,7 @@ class Server:
     def add_fragment(self, circuit: Circuit, ham: Hamiltonian, init_bits=None, chi_max: int = 64,
                      precision: str = "fp32", trunc_rel: float = 1e-5, svd_fp64: bool = False,
                      tensor_cores: bool = False) -> int:
-        cfg = Config(int(chi_max), PRECISIONS[precision], float(trunc_rel), 1 if svd_fp64 else 0, 0, 0.0,
+        cfg = Config(int(chi_max), PRECISIONS[precision], float(trunc_rel), int(svd_fp64), 0, 0.0,
                      1 if tensor_cores else 0)
         bits = None if init_bits is None else np.ascontiguousarray(init_bits, dtype=np.uint8)
         out = ctypes.c_int32()
