@@ -24,6 +24,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# Concurrent evaluations run one stream each; the default of 8 hardware work
+# queues would serialise streams beyond the eighth.  Read at CUDA context
+# creation, so it is set before torch initialises CUDA.
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 import numpy as np  # noqa: E402
 
@@ -266,9 +270,8 @@ def run_gpu(args):
     from paper_2303_03681_gb300 import mps
 
     w = build_workload(args.workload, args, rank)
-    if args.svd is None:
-        args.svd = "fp64" if w["precision"] == "fp64" else "fp32"
-    svd64 = args.svd == "fp64"
+    svd_mode = {"fp32": 0, "fp64": 1, "fp64-all": 2}[args.svd]
+    svd64 = svd_mode != 0
     B = args.batch
     main_stream = torch.cuda.current_stream()
     streams = [torch.cuda.Stream(device=dev) for _ in range(B)]
@@ -276,7 +279,7 @@ def run_gpu(args):
     H = mps.Hamiltonian(ctxs[0], w["ham"])
     C = mps.Circuit(ctxs[0], w["tmpl"])
     states = [mps.State(c, w["tmpl"].n_qubits, w["bits"], chi_max=w["chi"], precision=w["precision"],
-                        trunc_rel=w["trunc"], svd_fp64=svd64, tensor_cores=args.tensor_cores) for c in ctxs]
+                        trunc_rel=w["trunc"], svd_fp64=svd_mode, tensor_cores=args.tensor_cores) for c in ctxs]
     n_steps = args.warmup + args.steps
     n_par = max(1, w["tmpl"].n_params)
     thetas = thetas_for(w, (n_steps + args.steps) * B, rank_seed(rank))
@@ -313,6 +316,8 @@ def run_gpu(args):
     dominant = max(prof, key=lambda k: prof[k][2])
     for c in ctxs:
         c.profile([dominant])
+    for c in ctxs:
+        c.profile_read(reset=True)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -359,7 +364,11 @@ def run_gpu(args):
         per_step = dom_timed / args.steps
         if dominant == "svd":
             dt = "f64" if svd64 else "f32"
-            flops_per_launch = sum(r["svd_flops"] for r in reps) / max(1, sum(r["two_qubit_gates"] for r in reps))
+            # the bound is the FP64 units when any sweep runs in FP64: count the FP64 sweeps' share of the flops
+            sw32 = sum(r["svd_sweeps_fp32"] for r in reps)
+            sw64 = sum(r["svd_sweeps_fp64"] for r in reps)
+            share = (sw64 / max(1, sw32 + sw64)) if svd64 else 1.0
+            flops_per_launch = share * sum(r["svd_flops"] for r in reps) / max(1, sum(r["two_qubit_gates"] for r in reps))
             achieved = flops_per_launch / avg_s / 1e12
             peak = ALU_PEAK_TFLOPS[dt]
             roofline = {"bound": "alu", "kernel": "svd (Jacobi, cluster or single CTA)", "achieved": achieved,
@@ -368,7 +377,8 @@ def run_gpu(args):
                         "avg_launch_us": avg_s * 1e6, "launches_per_step": per_step,
                         "peak_source": f"derived {dt.upper()} ALU peak: {SM_COUNT} SMs x "
                                        f"{'128' if dt == 'f32' else '2'} FMA/clk x {SM_MHZ:.0f} MHz",
-                        "work": "Jacobi flops run (sweeps x pairs x per-pair dot and rotation flops) per launch",
+                        "work": (f"{dt.upper()} Jacobi flops run per launch (sweeps x pairs x per-pair dot and "
+                                 f"rotation flops; {sw32} FP32 and {sw64} FP64 sweeps in the last step)"),
                         "aggregate_achieved": flops_per_launch * per_step / (total_s / args.steps) / 1e12}
         else:
             roofline = {"bound": "alu", "kernel": dominant, "achieved": None, "peak": None, "unit": "TFLOP/s",
@@ -378,8 +388,13 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64" if w["precision"] == "fp32" else "c128",
         "data": "synthetic",
-        "config": dict(w["desc"], precision=f"{w['precision']} storage/contractions, {args.svd} Jacobi SVD, "
-                                            f"FP64 energy sum",
+        "config": dict(w["desc"], precision=(f"{w['precision']} storage/contractions, "
+                                             + {"fp32": "FP32 Jacobi SVD",
+                                                "fp64": ("FP64-accurate Jacobi SVD (FP32 sweeps, FP64 re-orthonormalisation,"
+                                                         " FP64 sweeps)" if w["precision"] == "fp32" else
+                                                         "FP64 Jacobi SVD"),
+                                                "fp64-all": "FP64 Jacobi SVD"}[args.svd]
+                                             + ", FP64 energy sum"),
                        contractions=("tcgen05 TF32 hi/lo split, 4 products" if args.tensor_cores and w["precision"] == "fp32"
                                      else "CUDA cores"),
                        batch=f"{B} concurrent evaluations per step (one stream each)",
@@ -414,7 +429,7 @@ def serve_phase(mps, device, C, H, w, args, rate):
     throughput) against a continuous-batching server with --batch slots."""
     srv = mps.Server(device, max_slots=args.batch)
     frag = srv.add_fragment(C, H, w["bits"], chi_max=w["chi"], precision=w["precision"], trunc_rel=w["trunc"],
-                            svd_fp64=(args.svd == "fp64"), tensor_cores=args.tensor_cores)
+                            svd_fp64={"fp32": 0, "fp64": 1, "fp64-all": 2}[args.svd], tensor_cores=args.tensor_cores)
     rng = make_rng(MASTER_SEED + 77)
     gaps = rng.exponential(1.0 / max(rate, 1e-6), args.serve_requests)
     thetas = thetas_for(w, args.serve_requests, MASTER_SEED + 78)
@@ -451,18 +466,19 @@ def merge_profiles(profs):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="c2")
     ap.add_argument("--excitations", type=int, default=100)
     ap.add_argument("--trunc-rel", type=float, default=1e-5)
     ap.add_argument("--precision", choices=["fp32", "fp64"], default=None)
-    ap.add_argument("--svd", choices=["fp32", "fp64"], default=None,
-                    help="Jacobi SVD precision (default: fp64 for complex128 states, fp32 for complex64)")
+    ap.add_argument("--svd", choices=["fp32", "fp64", "fp64-all"], default="fp64",
+                    help="Jacobi SVD: fp64 = FP64-accurate (complex64 states: FP32 sweeps, then FP64 ones), "
+                         "fp64-all = every sweep in FP64, fp32 = FP32 sweeps only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch", type=int, default=1, help="concurrent evaluations per step")
-    ap.add_argument("--tensor-cores", type=int, choices=[0, 1], default=0,
+    ap.add_argument("--batch", type=int, default=16, help="concurrent evaluations per step")
+    ap.add_argument("--tensor-cores", type=int, choices=[0, 1], default=1,
                     help="complex64 environment contractions on tcgen05 (1) or CUDA cores (0)")
     ap.add_argument("--serve-requests", type=int, default=0,
                     help="after the timed steps, serve this many Poisson-arriving requests (p50/p99 latency)")

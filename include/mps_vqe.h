@@ -149,6 +149,16 @@ mps_status mps_ctx_bytes_allocated(const mps_ctx* ctx, size_t* out);
 /* Destroys the context and frees its device memory.  Destroy its states,
  * Hamiltonians and circuits first: their handles become invalid. */
 void mps_ctx_destroy(mps_ctx* ctx);
+/* Circuit replay as CUDA graphs (default on).  With graphs on, the first
+ * mps_apply_circuit_async / vqe_eval / vqe_eval_batch of a (state, circuit)
+ * pair captures the bind kernel and every gate launch into a graph on the
+ * context's stream; later calls copy theta in and replay the graph, so the
+ * host issues one launch per circuit instead of three per gate.  A new
+ * circuit, a grown theta workspace or a changed profiling mask re-captures.
+ * enable = 0 launches every kernel from the host.  The results are the same
+ * either way.  Returns MPS_EINVAL for a NULL context. */
+mps_status mps_ctx_set_graphs(mps_ctx* ctx, int32_t enable);
+
 /* Kernel timing: for every kernel class whose bit is set in `mask`
  * (bit k = mps_kernel_kind k) the library brackets each launch with CUDA
  * events on the context stream.  Launch counts are always kept. */

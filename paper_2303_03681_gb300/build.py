@@ -60,7 +60,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
                 print(err, file=sys.stderr)
     if force or jobs or _newer(LIB, objs):
         tmp = LIB + ".tmp"
-        run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"])
+        run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcuda", "-lpthread"])
         os.replace(tmp, LIB)
     return LIB
 

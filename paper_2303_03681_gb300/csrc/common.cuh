@@ -131,11 +131,17 @@ struct SvdParams {
 // alpha = a_i^H a_i, beta = a_j^H a_j, g = gr + i gi = a_i^H a_j (Algorithm 1
 // of the paper, with the phase of g moved onto column j): the new columns are
 // a_i' = c a_i - conj(s e^{i phi}) a_j and a_j' = c a_j + s e^{i phi} a_i.
-// Returns false when the pair is left alone (already orthogonal to tol, or a
-// column at the rounding floor).
+// Returns false when the pair is left alone: already orthogonal to tol, a
+// column at the rounding floor, or both columns with squared norm <= tau2.
+// With tau2 = eps_rel^2 ||A||_F^2 / n^2 (n columns) the columns below it
+// hold at most eps_rel^2 ||A||_F^2 / n <= (eps_rel s_1)^2 together, so
+// whatever their mutual angles, their singular values fall below the
+// truncation threshold eps_rel s_1; they only have to be orthogonalised
+// against the larger columns, which stay exact.
 template <typename S>
-__device__ __forceinline__ bool jacobi_rotation(S alpha, S beta, S gr, S gi, S tol, S floor, S tiny, S& c,
+__device__ __forceinline__ bool jacobi_rotation(S alpha, S beta, S gr, S gi, S tol, S floor, S tiny, S tau2, S& c,
                                                 cplx<S>& sph) {
+  if (!(max(alpha, beta) > tau2)) return false;
   const S mag = sqrt(gr * gr + gi * gi);
   if (!(mag > tiny) || !(mag > tol * sqrt(alpha * beta)) || !(min(alpha, beta) > floor)) return false;
   const S zeta = (beta - alpha) / (S(2) * mag);
@@ -155,7 +161,9 @@ __device__ __forceinline__ bool jacobi_rotation(S alpha, S beta, S gr, S gi, S t
 // an extra sweep: a pair left with |g| ~ 1e-7 |g| is rotated again.
 template <>
 __device__ __forceinline__ bool jacobi_rotation<double>(double alpha, double beta, double gr, double gi, double tol,
-                                                        double floor, double tiny, double& c, cplx<double>& sph) {
+                                                        double floor, double tiny, double tau2, double& c,
+                                                        cplx<double>& sph) {
+  if (!(max(alpha, beta) > tau2)) return false;
   const double mag2 = gr * gr + gi * gi;
   if (!(mag2 > tiny) || !(mag2 > tol * tol * alpha * beta) || !(min(alpha, beta) > floor)) return false;
   // 2^-h with 2^(2h) ~ mag2 (mag2 is a normal double here)

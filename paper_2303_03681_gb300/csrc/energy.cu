@@ -4,6 +4,8 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <string>
+#include <thread>
 #include <unordered_map>
 
 #include "gate_kernels.cuh"
@@ -183,6 +185,10 @@ static mps_status ensure_env_buffers(const std::vector<int>& chi, mps_state* st,
   return MPS_OK;
 }
 
+// Smallest bond dimension (either side of a site) whose environment
+// contractions go to the tensor cores when a state allows them.
+constexpr int kTcMinChi = 64;
+
 // Tensor-core path of one level (complex64 only).  Returns false if a launch failed.
 template <typename R>
 static bool launch_env_tc(mps_state*, mps_ham*, const LevelHost&, int, const std::vector<int>&, const cplx<R>*,
@@ -280,9 +286,11 @@ static mps_status energy_levels(mps_state* st, mps_ham* h, double* d_out) {
     lv.cap_r = chi[j + 1];
     const cplx<R>* Bj = B + st->site_off[j];
     const int tl = (lv.cap_l + kTile - 1) / kTile, tr = (lv.cap_r + kTile - 1) / kTile;
-    if (st->tc) {
+    if (st->tc && std::max(chi[j], chi[j + 1]) >= kTcMinChi) {
       // complex64 on the tensor cores: diagonal parents by scaling, stored
-      // environments and children as batched tcgen05 complex GEMMs
+      // environments and children as batched tcgen05 complex GEMMs (below
+      // kTcMinChi a 128-row tile is mostly padding and the CUDA-core
+      // kernels are faster)
       if (!launch_env_tc<R>(st, h, L, j, chi, Lprev, Bj, M, Lcur)) {
         set_error("energy: tensor-core launch failed: %s", cudaGetErrorString(cudaGetLastError()));
         return MPS_ECUDA;
@@ -552,26 +560,66 @@ static mps_status run_batch(const vqe_request* reqs, size_t n, double* energies_
       rc[i] = MPS_EINVAL;
     }
   }
-  // reset + bind on every request's own stream
-  for (size_t i = 0; i < n; ++i) {
-    if (rc[i] != MPS_OK) continue;
-    const vqe_request& r = reqs[i];
-    DeviceGuard guard(r.state->ctx->device);
-    rc[i] = state_reset(r.state, r.init_bits);
-    if (rc[i] == MPS_OK) rc[i] = state_bind_circuit(r.state, r.circuit, r.theta, on_device ? 1 : 0);
-  }
-  // gates round-robin across requests
-  int max_gates = 0;
-  for (size_t i = 0; i < n; ++i)
-    if (rc[i] == MPS_OK) max_gates = std::max(max_gates, reqs[i].circuit->n_gates);
-  for (int g = 0; g < max_gates; ++g) {
+  // Reset, bind and gates.  The requests are grouped by context (a
+  // context's stream and bookkeeping belong to one host thread) and the
+  // groups are fed by up to 16 host threads, each going round-robin over
+  // its requests gate by gate, so the host's launch rate does not cap the
+  // number of evaluations in flight.
+  std::vector<std::vector<size_t>> groups;
+  {
+    std::vector<mps_ctx*> keys;
     for (size_t i = 0; i < n; ++i) {
-      const vqe_request& r = reqs[i];
-      if (rc[i] != MPS_OK || g >= r.circuit->n_gates) continue;
-      DeviceGuard guard(r.state->ctx->device);
-      rc[i] = state_apply_device_gates(r.state, r.state->d_bound + g, &r.circuit->q[g], &r.circuit->arity[g], 1);
-      if (rc[i] != MPS_OK) r.state->broken = true;
+      if (rc[i] != MPS_OK) continue;
+      mps_ctx* c = reqs[i].state->ctx;
+      size_t gi = 0;
+      while (gi < keys.size() && keys[gi] != c) ++gi;
+      if (gi == keys.size()) {
+        keys.push_back(c);
+        groups.emplace_back();
+      }
+      groups[gi].push_back(i);
     }
+  }
+  const size_t hw = std::max(1u, std::thread::hardware_concurrency());
+  const size_t n_threads = std::min<size_t>({groups.size(), std::max<size_t>(1, hw / 2), 16});
+  std::vector<std::string> errs(n_threads);
+  auto work = [&](size_t t) {
+    std::vector<size_t> mine;
+    for (size_t gi = t; gi < groups.size(); gi += n_threads)
+      for (size_t i : groups[gi]) mine.push_back(i);
+    for (size_t i : mine) {
+      const vqe_request& r = reqs[i];
+      DeviceGuard guard(r.state->ctx->device);
+      rc[i] = state_reset(r.state, r.init_bits);
+      if (rc[i] == MPS_OK) rc[i] = state_bind_circuit(r.state, r.circuit, r.theta, on_device ? 1 : 0);
+    }
+    int max_gates = 0;
+    for (size_t i : mine)
+      if (rc[i] == MPS_OK) max_gates = std::max(max_gates, reqs[i].circuit->n_gates);
+    for (int g = 0; g < max_gates; ++g) {
+      for (size_t i : mine) {
+        const vqe_request& r = reqs[i];
+        if (rc[i] != MPS_OK || g >= r.circuit->n_gates) continue;
+        DeviceGuard guard(r.state->ctx->device);
+        rc[i] = state_apply_device_gates(r.state, r.state->d_bound + g, &r.circuit->q[g], &r.circuit->arity[g], 1);
+        if (rc[i] != MPS_OK) r.state->broken = true;
+      }
+    }
+    for (size_t i : mine)
+      if (rc[i] != MPS_OK && errs[t].empty()) errs[t] = last_error();
+  };
+  if (n_threads <= 1) {
+    if (!groups.empty()) work(0);
+  } else {
+    std::vector<std::thread> pool;
+    for (size_t t = 1; t < n_threads; ++t) pool.emplace_back(work, t);
+    work(0);
+    for (auto& th : pool) th.join();
+    for (auto& e : errs)
+      if (!e.empty()) {
+        set_error("%s", e.c_str());
+        break;
+      }
   }
   // energies (each reads its bond dimensions once), then the results
   std::vector<int> tc_flag(n, 0);

@@ -159,7 +159,8 @@ template <> struct SvdEps<float> {
 // are left alone: rotating two of them only reshuffles rounding noise, and a
 // rotation against a larger column would move it by less than that noise.
 template <typename S>
-__device__ int jacobi_sweeps(cplx<S>* A, cplx<S>* V, int m, int n, int max_sweeps, S tol, S floor, int* s_flag) {
+__device__ int jacobi_sweeps(cplx<S>* A, cplx<S>* V, int m, int n, int max_sweeps, S tol, S floor, S tau2,
+                             int* s_flag) {
   using C = cplx<S>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int nn = n + (n & 1);
@@ -191,7 +192,7 @@ __device__ int jacobi_sweeps(cplx<S>* A, cplx<S>* V, int m, int n, int max_sweep
         gam.y = warp_sum(gam.y);
         S c;
         C sph;  // s e^{i phi}
-        if (!jacobi_rotation<S>(alpha, beta, gam.x, gam.y, tol, floor, tiny, c, sph)) continue;
+        if (!jacobi_rotation<S>(alpha, beta, gam.x, gam.y, tol, floor, tiny, tau2, c, sph)) continue;
         rotated = true;
         for (int row = lane; row < m; row += 32) {
           const C x = ai[row], y = aj[row];
@@ -273,7 +274,8 @@ __global__ void __launch_bounds__(1024, 1)
   const double fro2 = s_nrm;
   const S floor = S(16.0 * double(SvdEps<S>::unit()) * double(SvdEps<S>::unit()) * fro2);
   __syncthreads();
-  const int sweeps = jacobi_sweeps<S>(A, V, m, n, p.max_sweeps, tol, floor, &s_flag);
+  const S tau2 = S(p.trunc_rel * p.trunc_rel * fro2 / (double(n) * double(n)));
+  const int sweeps = jacobi_sweeps<S>(A, V, m, n, p.max_sweeps, tol, floor, tau2, &s_flag);
 
   // sigma_j = ||A_j|| (Algorithm 1: column norms)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;

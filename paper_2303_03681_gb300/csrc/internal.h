@@ -37,6 +37,24 @@ struct DeviceGuard {
   }
 };
 
+// A circuit's bind + gate launches captured once for one state and replayed
+// as a CUDA graph.  Kernel timing inside the graph uses events owned by the
+// graph (re-recorded by every replay).
+struct CircuitGraph {
+  uint64_t circ_serial = 0;
+  const void* theta_ptr = nullptr;
+  const void* bound_ptr = nullptr;
+  uint32_t mask = 0;
+  cudaGraphExec_t exec = nullptr;
+  struct Timing {
+    int kind;
+    cudaEvent_t a, b;
+  };
+  std::vector<Timing> timing;
+  long long counts[MPS_K_COUNT] = {};  // launches per replay
+  long long unread = 0;                // replays since the last profile collection
+};
+
 }  // namespace mpsv
 
 struct mps_ctx {
@@ -57,6 +75,9 @@ struct mps_ctx {
   };
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
+  bool use_graphs = true;                           // replay circuits as CUDA graphs (mps_ctx_set_graphs)
+  mpsv::CircuitGraph* capturing = nullptr;          // graph being captured on this context's stream
+  std::vector<mpsv::CircuitGraph*> graph_watch;     // graphs replayed since the last profile collection
 };
 
 namespace mpsv {
@@ -113,10 +134,12 @@ struct mps_state {
   double* d_vals = nullptr;
   size_t vals_cap = 0;
   double* d_energy = nullptr;
+  mpsv::CircuitGraph* graph = nullptr;  // last captured circuit (graph replay)
 };
 
 struct mps_circuit {
   mps_ctx* ctx = nullptr;
+  uint64_t serial = 0;  // unique per created circuit (graph cache key)
   int n = 0;
   int n_params = 0;
   int n_gates = 0;
@@ -155,6 +178,10 @@ mps_status state_apply_device_gates(mps_state* st, const DevGate* d_gates, const
 mps_status state_reset(mps_state* st, const uint8_t* bits);
 // Copies theta into the state's workspace and binds the circuit's gates there.
 mps_status state_bind_circuit(mps_state* st, const mps_circuit* c, const double* theta, int theta_on_device);
+// Binds theta and applies the whole circuit: a CUDA graph captured on first
+// use for this (state, circuit) and replayed afterwards.
+mps_status state_run_circuit(mps_state* st, const mps_circuit* c, const double* theta, int theta_on_device);
+void graph_destroy(mps_ctx* ctx, CircuitGraph* g);
 // energy.cu
 mps_status ham_energy_async(mps_state* st, mps_ham* h, double* d_out);
 }  // namespace mpsv

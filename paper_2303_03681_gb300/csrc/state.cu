@@ -1,5 +1,6 @@
 // Contexts, states, gates and circuit templates of libmpsvqe.
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <mutex>
 
@@ -58,6 +59,19 @@ void dev_free(mps_ctx* ctx, void* p) {
 }
 
 KernelScope::KernelScope(mps_ctx* ctx, int k) : c(ctx), kind(k) {
+  if (c->capturing) {
+    // inside a graph capture: counted per replay, timed with the graph's own events
+    c->capturing->counts[k] += 1;
+    if (!(c->prof_mask & (1u << k))) return;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      cudaGetLastError();
+      if (a) cudaEventDestroy(a);
+      a = b = nullptr;
+      return;
+    }
+    cudaEventRecordWithFlags(a, c->stream, cudaEventRecordExternal);  // an event-record node of the graph
+    return;
+  }
   c->launches[k] += 1;
   if (!(c->prof_mask & (1u << k))) return;
   for (cudaEvent_t* e : {&a, &b}) {
@@ -73,6 +87,13 @@ KernelScope::KernelScope(mps_ctx* ctx, int k) : c(ctx), kind(k) {
 }
 
 KernelScope::~KernelScope() {
+  if (c->capturing) {
+    if (a && b) {
+      cudaEventRecordWithFlags(b, c->stream, cudaEventRecordExternal);
+      c->capturing->timing.push_back({kind, a, b});
+    }
+    return;
+  }
   if (!a || !b) {
     if (a) c->pool.push_back(a);
     if (b) c->pool.push_back(b);
@@ -95,6 +116,37 @@ static void collect_profile(mps_ctx* c) {
     c->pool.push_back(p.b);
   }
   c->pending.clear();
+  // graph replays: the events hold the last replay's times, taken for every
+  // replay since the previous collection
+  for (CircuitGraph* g : c->graph_watch) {
+    if (g->unread <= 0) continue;
+    for (auto& t : g->timing) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+        c->ms[t.kind] += (double)ms * g->unread;
+        c->timed[t.kind] += g->unread;
+      } else {
+        cudaGetLastError();
+      }
+    }
+    g->unread = 0;
+  }
+  c->graph_watch.clear();
+}
+
+void graph_destroy(mps_ctx* c, CircuitGraph* g) {
+  if (!g) return;
+  for (size_t i = 0; i < c->graph_watch.size(); ++i)
+    if (c->graph_watch[i] == g) {
+      c->graph_watch.erase(c->graph_watch.begin() + i);
+      break;
+    }
+  for (auto& t : g->timing) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  delete g;
 }
 
 static int bond_cap(int b, int n, int chi_max) {
@@ -179,6 +231,22 @@ template <typename S, typename R> static SvdPlan cluster_svd_plan(int mcap, int 
     max16 = n;
   });
   const size_t lim = max_dyn_smem() - 2048;
+  if constexpr (sizeof(S) == 4) {
+    // FP32 pair steps are latency-bound: few CTAs (fewer rounds and cluster
+    // barriers) with 16 warps each, so that concurrent evaluations find SMs
+    // free.  Columns stay in shared memory whenever the actual sizes fit.
+    const int P = 4, b = (ncap + 2 * P - 1) / (2 * P);
+    pl.P = P;
+    pl.threads = 512;
+    ClusterSvdSmem<S> L(b, mcap + ncap, 2 * P * b, pl.threads);
+    if (L.total <= lim) {
+      pl.smem = L.total;
+    } else {
+      pl.global = true;
+      pl.smem = std::min(lim, std::max(ClusterSvdSmem<S>(b, 0, 2 * P * b, pl.threads).total, (size_t)160 * 1024));
+    }
+    return pl;
+  } else {
   for (int P = ncap < 64 ? 4 : ((ncap >= 192 && max16 > 0) ? 16 : 8); P <= 16; P *= 2) {
     if (P == 16 && max16 <= 0) break;
     const int b = (ncap + 2 * P - 1) / (2 * P);
@@ -197,6 +265,7 @@ template <typename S, typename R> static SvdPlan cluster_svd_plan(int mcap, int 
   pl.global = true;
   pl.smem = std::min(lim, std::max(ClusterSvdSmem<S>(b, 0, 2 * P * b, pl.threads).total, (size_t)96 * 1024));
   return pl;
+  }
 }
 
 template <typename R, typename S>
@@ -331,7 +400,8 @@ mps_status state_reset(mps_state* st, const uint8_t* bits) {
   return MPS_OK;
 }
 
-mps_status state_bind_circuit(mps_state* st, const mps_circuit* c, const double* theta, int theta_on_device) {
+// Workspace for the bound gates and theta, and theta copied in (stream-ordered).
+static mps_status state_upload_theta(mps_state* st, const mps_circuit* c, const double* theta, int theta_on_device) {
   mps_ctx* ctx = st->ctx;
   cudaStream_t s = ctx->stream;
   if ((size_t)c->n_gates > st->bound_cap) {
@@ -353,11 +423,87 @@ mps_status state_bind_circuit(mps_state* st, const mps_circuit* c, const double*
   if (c->n_params)
     MPSV_CUDA(cudaMemcpyAsync(st->d_theta, theta, c->n_params * sizeof(double),
                               theta_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
-  if (c->n_gates) {
-    KernelScope k(ctx, MPS_K_SETUP);
-    bind_kernel<<<c->n_gates, 32, 0, s>>>(c->d_tmpl, c->n_gates, st->d_theta, st->d_bound);
-  }
+  return MPS_OK;
+}
+
+static void launch_bind(mps_state* st, const mps_circuit* c) {
+  if (!c->n_gates) return;
+  KernelScope k(st->ctx, MPS_K_SETUP);
+  bind_kernel<<<c->n_gates, 32, 0, st->ctx->stream>>>(c->d_tmpl, c->n_gates, st->d_theta, st->d_bound);
+}
+
+mps_status state_bind_circuit(mps_state* st, const mps_circuit* c, const double* theta, int theta_on_device) {
+  mps_status rc = state_upload_theta(st, c, theta, theta_on_device);
+  if (rc != MPS_OK) return rc;
+  launch_bind(st, c);
   MPSV_CUDA(cudaGetLastError());
+  return MPS_OK;
+}
+
+// One-time launch attributes (shared-memory opt-ins, the 16-CTA cluster
+// occupancy query) set before a capture, outside it.
+template <typename R, typename S> static void prime_launch_attrs() {
+  svd_set_attr<S, R>();
+  (void)cluster_svd_plan<S, R>(256, 256);
+}
+
+static void prime_launch_attrs(const mps_state* st) {
+  if (st->fp32)
+    st->svd64 ? prime_launch_attrs<float, double>() : prime_launch_attrs<float, float>();
+  else
+    st->svd64 ? prime_launch_attrs<double, double>() : prime_launch_attrs<double, float>();
+}
+
+mps_status state_run_circuit(mps_state* st, const mps_circuit* c, const double* theta, int theta_on_device) {
+  mps_ctx* ctx = st->ctx;
+  cudaStream_t s = ctx->stream;
+  mps_status rc = state_upload_theta(st, c, theta, theta_on_device);
+  if (rc != MPS_OK || !c->n_gates) return rc;
+  if (!ctx->use_graphs) {
+    launch_bind(st, c);
+    return state_apply_device_gates(st, st->d_bound, c->q.data(), c->arity.data(), c->n_gates);
+  }
+  CircuitGraph* g = st->graph;
+  const bool hit = g && g->exec && g->circ_serial == c->serial && g->theta_ptr == st->d_theta &&
+                   g->bound_ptr == st->d_bound && g->mask == ctx->prof_mask;
+  if (!hit) {
+    if (g) {
+      MPSV_CUDA(cudaStreamSynchronize(s));
+      collect_profile(ctx);
+      graph_destroy(ctx, g);
+      st->graph = nullptr;
+    }
+    g = new CircuitGraph();
+    g->circ_serial = c->serial;
+    g->theta_ptr = st->d_theta;
+    g->bound_ptr = st->d_bound;
+    g->mask = ctx->prof_mask;
+    prime_launch_attrs(st);
+    cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+      delete g;
+      return cuda_fail(e, "cudaStreamBeginCapture");
+    }
+    ctx->capturing = g;
+    launch_bind(st, c);
+    rc = state_apply_device_gates(st, st->d_bound, c->q.data(), c->arity.data(), c->n_gates);
+    ctx->capturing = nullptr;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(s, &graph);
+    if (rc == MPS_OK && e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != MPS_OK || e != cudaSuccess) {
+      graph_destroy(ctx, g);
+      return rc != MPS_OK ? rc : cuda_fail(e, "circuit graph capture");
+    }
+    st->graph = g;
+  }
+  MPSV_CUDA(cudaGraphLaunch(g->exec, s));
+  g->unread += 1;
+  for (int k = 0; k < MPS_K_COUNT; ++k) ctx->launches[k] += g->counts[k];
+  bool watched = false;
+  for (CircuitGraph* w : ctx->graph_watch) watched |= (w == g);
+  if (!watched) ctx->graph_watch.push_back(g);
   return MPS_OK;
 }
 
@@ -366,6 +512,11 @@ static void destroy_state(mps_state* st) {
   mps_ctx* c = st->ctx;
   DeviceGuard guard(c->device);
   cudaStreamSynchronize(c->stream);
+  if (st->graph) {
+    collect_profile(c);
+    graph_destroy(c, st->graph);
+    st->graph = nullptr;
+  }
   for (void* p : {st->d_B, (void*)st->d_lam, (void*)st->d_chi, (void*)st->d_site_off, (void*)st->d_lam_off,
                   (void*)st->d_bits, (void*)st->d_rep, st->d_C, st->d_A, st->d_V, (void*)st->d_gates,
                   (void*)st->d_bound, (void*)st->d_theta, st->d_L[0], st->d_L[1], st->d_M, (void*)st->d_vals,
@@ -448,6 +599,15 @@ mps_status mps_ctx_bytes_allocated(const mps_ctx* ctx, size_t* out) {
     return MPS_EINVAL;
   }
   *out = ctx->allocated;
+  return MPS_OK;
+}
+
+mps_status mps_ctx_set_graphs(mps_ctx* ctx, int32_t enable) {
+  if (!ctx) {
+    set_error("mps_ctx_set_graphs: NULL context");
+    return MPS_EINVAL;
+  }
+  ctx->use_graphs = enable != 0;
   return MPS_OK;
 }
 
@@ -748,7 +908,9 @@ mps_status mps_circuit_create(mps_ctx* ctx, int32_t n_qubits, const mps_template
     return MPS_EINVAL;
   }
   std::vector<DevTmplGate> ht(n_gates);
+  static std::atomic<uint64_t> next_serial{1};
   auto* c = new mps_circuit();
+  c->serial = next_serial++;
   c->ctx = ctx;
   c->n = n_qubits;
   c->n_params = n_params;
@@ -816,8 +978,7 @@ mps_status mps_apply_circuit_async(mps_state* st, const mps_circuit* c, const do
     return MPS_ESTATE;
   }
   DeviceGuard guard(st->ctx->device);
-  mps_status rc = state_bind_circuit(st, c, theta, theta_on_device);
-  if (rc == MPS_OK && c->n_gates) rc = state_apply_device_gates(st, st->d_bound, c->q.data(), c->arity.data(), c->n_gates);
+  mps_status rc = state_run_circuit(st, c, theta, theta_on_device);
   if (rc != MPS_OK) st->broken = true;
   return rc;
 }

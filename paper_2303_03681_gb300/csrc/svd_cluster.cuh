@@ -72,7 +72,7 @@ __device__ __forceinline__ void warp_sum4(S& a, S& b, S& c, S& d) {
 // entries use the first m (A) rows.
 template <typename S>
 __device__ __forceinline__ int jacobi_pair_smem(cplx<S>* ai, cplx<S>* aj, int m, int len, int lane, S tol, S floor,
-                                                S tiny) {
+                                                S tiny, S tau2) {
   using C = cplx<S>;
   S alpha = 0, beta = 0, gr = 0, gi = 0;
   for (int r = lane; r < m; r += 32) {
@@ -85,7 +85,7 @@ __device__ __forceinline__ int jacobi_pair_smem(cplx<S>* ai, cplx<S>* aj, int m,
   warp_sum4(alpha, beta, gr, gi);
   S c;
   C sph;
-  if (!jacobi_rotation(alpha, beta, gr, gi, tol, floor, tiny, c, sph)) return 0;
+  if (!jacobi_rotation(alpha, beta, gr, gi, tol, floor, tiny, tau2, c, sph)) return 0;
   for (int r = lane; r < len; r += 32) {
     const C x = ai[r], y = aj[r];
     ai[r] = csub(cmk<S>(c * x.x, c * x.y), cmulc(sph, y));
@@ -97,7 +97,7 @@ __device__ __forceinline__ int jacobi_pair_smem(cplx<S>* ai, cplx<S>* aj, int m,
 // Same with the first column in registers: x[i] is row lane + 32 i.
 template <typename S>
 __device__ __forceinline__ int jacobi_pair_reg(cplx<S> (&x)[kClusterRegs], cplx<S>* aj, int m, int len, int lane,
-                                               S tol, S floor, S tiny) {
+                                               S tol, S floor, S tiny, S tau2) {
   using C = cplx<S>;
   S alpha = 0, beta = 0, gr = 0, gi = 0;
 #pragma unroll
@@ -114,7 +114,7 @@ __device__ __forceinline__ int jacobi_pair_reg(cplx<S> (&x)[kClusterRegs], cplx<
   warp_sum4(alpha, beta, gr, gi);
   S c;
   C sph;
-  if (!jacobi_rotation(alpha, beta, gr, gi, tol, floor, tiny, c, sph)) return 0;
+  if (!jacobi_rotation(alpha, beta, gr, gi, tol, floor, tiny, tau2, c, sph)) return 0;
 #pragma unroll
   for (int i = 0; i < kClusterRegs; ++i) {
     const int r = lane + 32 * i;
@@ -181,7 +181,7 @@ struct ColStore {
 // cluster barriers in step).  Returns the sweeps run.
 template <typename T, int kOp>
 __device__ int cluster_sweeps(const ClusterGeom& g, const ColStore<T>& cs, int& cur, int max_sweeps, T tol, T floor,
-                              T tiny, bool& converged, const cg::cluster_group& cluster, int* s_flag_in,
+                              T tiny, T tau2, bool& converged, const cg::cluster_group& cluster, int* s_flag_in,
                               int* s_any) {
   using C = cplx<T>;
   // In the cross rounds, when every warp has one top-slot column, warp w
@@ -213,7 +213,7 @@ __device__ int cluster_sweeps(const ClusterGeom& g, const ColStore<T>& cs, int& 
             C* x = cs.col(cur, a0 / g.b, a0 % g.b, rnd);
             C* y = cs.col(cur, a1 / g.b, a1 % g.b, rnd);
             if (kOp == 0)
-              rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tol, floor, tiny);
+              rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tol, floor, tiny, tau2);
             else
               orth_pair<T>(x, y, g.m, g.len, g.wl);
           }
@@ -233,13 +233,13 @@ __device__ int cluster_sweeps(const ClusterGeom& g, const ColStore<T>& cs, int& 
           if (cache_x) {
             if (active)
               rotated |= jacobi_pair_reg<T>(xr, cs.col(cur, 1, (g.wp + sr) % g.b, rnd), g.m, g.len, g.wl, tol,
-                                            floor, tiny);
+                                            floor, tiny, tau2);
           } else {
             for (int pw = g.wp; pw < g.b; pw += g.nw) {
               C* x = cs.col(cur, 0, pw, rnd);
               C* y = cs.col(cur, 1, (pw + sr) % g.b, rnd);
               if (kOp == 0)
-                rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tol, floor, tiny);
+                rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tol, floor, tiny, tau2);
               else
                 orth_pair<T>(x, y, g.m, g.len, g.wl);
             }
@@ -424,6 +424,8 @@ __global__ void __launch_bounds__(512, 1)
   // product); columns with squared norm below (4 u ||A||_F)^2 are rounding
   // noise and left alone.
   const double tol_scale = 4.0 * sqrt(double(max(m, ncols)));
+  // pairs of columns that end up below the truncation threshold together need no rotation
+  const double tau2 = p.trunc_rel * p.trunc_rel * fro2 / (double(ncols) * double(ncols));
   int cur = 0, used = 0, used32 = 0;
   bool converged = false;
   t_load = clock64();
@@ -433,8 +435,8 @@ __global__ void __launch_bounds__(512, 1)
     int cur32 = 0;
     bool conv32 = false;
     used32 = cluster_sweeps<float, 0>(g, cs32, cur32, p.max_sweeps, float(tol_scale) * u32,
-                                      float(16.0 * double(u32) * double(u32) * fro2), 1e-35f, conv32, cluster,
-                                      s_flag_in, &s_any);
+                                      float(16.0 * double(u32) * double(u32) * fro2), 1e-35f, float(tau2), conv32,
+                                      cluster, s_flag_in, &s_any);
     used = used32;
     t_lo = clock64();
     // FP64 columns: V promoted (A follows from the theta below)
@@ -449,7 +451,7 @@ __global__ void __launch_bounds__(512, 1)
     // overwrite them (in shared memory they share a buffer with FP64 ones)
     cluster.sync();
     bool dummy;
-    cluster_sweeps<S, 1>(g, cs, cur, 1, S(0), S(0), S(0), dummy, cluster, s_flag_in, &s_any);
+    cluster_sweeps<S, 1>(g, cs, cur, 1, S(0), S(0), S(0), S(0), dummy, cluster, s_flag_in, &s_any);
     // the diagonal of the first-order step: |v|^2 -> 1
     for (int c = g.wp; g.member && c < 2 * b; c += g.nw) {
       C* v = cs.col(cur, c / b, c % b, 0);
@@ -483,7 +485,8 @@ __global__ void __launch_bounds__(512, 1)
   const S tol = p.tol > 0 ? S(p.tol) : S(tol_scale) * eps_u;
   const S floor = S(16.0 * double(eps_u) * double(eps_u) * fro2);
   const S tiny = sizeof(S) == 8 ? S(1e-290) : S(1e-35f);
-  used += cluster_sweeps<S, 0>(g, cs, cur, p.max_sweeps, tol, floor, tiny, converged, cluster, s_flag_in, &s_any);
+  used += cluster_sweeps<S, 0>(g, cs, cur, p.max_sweeps, tol, floor, tiny, S(tau2), converged, cluster, s_flag_in,
+                               &s_any);
   const int sweep = used;
 
   // ---- singular values: norms of the A parts, shared with every CTA

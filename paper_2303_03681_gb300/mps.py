@@ -100,6 +100,7 @@ def _load():
                               ctypes.POINTER(SZ), ctypes.POINTER(SZ)], ctypes.c_int),
         "mps_server_destroy": ([P], None),
         "mps_ctx_profile": ([P, ctypes.c_uint32], ctypes.c_int),
+        "mps_ctx_set_graphs": ([P, I32], ctypes.c_int),
         "mps_ctx_profile_read": ([P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                   ctypes.POINTER(D), I32], ctypes.c_int),
     }
@@ -241,6 +242,10 @@ class Context:
 
     def set_alloc_limit(self, nbytes: int):
         _check(_lib.mps_ctx_set_alloc_limit(self.handle, int(nbytes)))
+
+    def set_graphs(self, enable: bool):
+        """Replay circuits as CUDA graphs (default) or launch every kernel from the host."""
+        _check(_lib.mps_ctx_set_graphs(self.handle, 1 if enable else 0))
 
     def profile(self, kinds=()):
         """Time every launch of the named kernel classes with CUDA events."""
