@@ -477,7 +477,7 @@ def main():
                     help="Jacobi SVD: fp64 = FP64-accurate (complex64 states: FP32 sweeps, then FP64 ones), "
                          "fp64-all = every sweep in FP64, fp32 = FP32 sweeps only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--batch", type=int, default=16, help="concurrent evaluations per step")
+    ap.add_argument("--batch", type=int, default=8, help="concurrent evaluations per step")
     ap.add_argument("--tensor-cores", type=int, choices=[0, 1], default=1,
                     help="complex64 environment contractions on tcgen05 (1) or CUDA cores (0)")
     ap.add_argument("--serve-requests", type=int, default=0,

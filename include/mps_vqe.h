@@ -237,11 +237,16 @@ typedef struct {
 mps_status vqe_eval(mps_ctx* ctx, const vqe_request* reqs, size_t n, double* energies_out,
                     mps_status* status_out);
 
-/* Batched form of vqe_eval (the paper's fragment-level parallelism, L298,
- * on one GPU): the requests may belong to different contexts, each with its
- * own stream, and must use distinct states.  The library issues their gates
- * round-robin (gate g of every request before gate g+1), so independent
- * evaluations overlap on the device; then it evaluates each energy.
+/* Batched form of vqe_eval (the fragment-level parallelism of the paper's
+ * Methods, "Heterogeneous parallelization strategy", on one GPU): the
+ * requests may belong to different contexts, each with its own stream, and
+ * must use distinct states.  Requests are grouped by context; up to 16 host
+ * threads issue the groups' gates, each going round-robin over its requests
+ * (gate g of every request before gate g+1), so independent evaluations
+ * overlap on the device; then the calling thread evaluates each energy.
+ * Streams beyond the device's hardware work queues are serialised by the
+ * driver: set CUDA_DEVICE_MAX_CONNECTIONS (up to 32) to at least the number
+ * of contexts before the process creates its CUDA context.
  * energies_out[i] / status_out[i] (host, status nullable) as in vqe_eval;
  * the return value is the first failing status, or MPS_OK. */
 mps_status vqe_eval_batch(const vqe_request* reqs, size_t n, double* energies_out, mps_status* status_out);
@@ -262,7 +267,8 @@ mps_status vqe_eval_batch_async(const vqe_request* reqs, size_t n, double* d_ene
  * hbm_budget_bytes (0 = no budget), issues every admitted evaluation's gates
  * a few at a time in turn (requests arriving while others run join between
  * gate groups), evaluates its energy and completes it.  This is the paper's
- * fragment-level parallelism (L298) mapped to one GPU.  The result of a
+ * fragment-level parallelism (Methods, "Heterogeneous parallelization
+ * strategy") mapped to one GPU.  The result of a
  * request does not depend on what else is in flight: the same kernels run on
  * the same data.  Handles passed to a server (circuit, Hamiltonian) must
  * outlive it. */

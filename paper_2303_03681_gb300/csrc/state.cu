@@ -214,7 +214,7 @@ template <typename S, typename R> static SvdPlan cluster_svd_plan(int mcap, int 
     cudaFuncSetAttribute(svd_cluster_kernel<S, R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(16);
-    cfg.blockDim = dim3(512);
+    cfg.blockDim = dim3(kClusterMaxThreads<S>);
     cfg.dynamicSmemBytes = max_dyn_smem() - 2048;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -253,7 +253,7 @@ template <typename S, typename R> static SvdPlan cluster_svd_plan(int mcap, int 
     ClusterSvdSmem<S> L(b, mcap + ncap, 2 * P * b, 32 * b);
     if (L.total <= lim && 32 * b <= 512) {
       pl.P = P;
-      pl.threads = 32 * b;
+      pl.threads = std::min(32 * b, kClusterMaxThreads<S>);
       pl.smem = L.total;
       return pl;
     }
@@ -261,7 +261,7 @@ template <typename S, typename R> static SvdPlan cluster_svd_plan(int mcap, int 
   const int P = max16 > 0 ? 16 : 8;
   const int b = (ncap + 2 * P - 1) / (2 * P);
   pl.P = P;
-  pl.threads = 32 * std::min(b, 16);
+  pl.threads = std::min(32 * b, kClusterMaxThreads<S>);
   pl.global = true;
   pl.smem = std::min(lim, std::max(ClusterSvdSmem<S>(b, 0, 2 * P * b, pl.threads).total, (size_t)96 * 1024));
   return pl;

@@ -159,19 +159,24 @@ struct ClusterGeom {
 };
 
 // Stacked columns of one precision: shared-memory ping-pong slots
-// [pp][slot][c][len], or (sm == nullptr) 2P global blocks [block][c][len]
-// that stay put while the round robin renames positions.
-template <typename T>
+// [pp][slot][c][len], or 2P global blocks [block][c][len] that stay put while
+// the round robin renames positions.
+// The layout is a template parameter so that the shared-memory form's
+// pointers stay shared-memory pointers for the compiler (shared loads and
+// stores rather than generic ones).
+template <typename T, bool kGlobal>
 struct ColStore {
-  cplx<T>* sm;
-  cplx<T>* gm;
+  cplx<T>* base;  // shared-memory slots, or the global blocks
   int b, len, P, me;
   __device__ cplx<T>* col(int pp, int slot, int c, int rnd) const {
-    if (sm) return sm + ((size_t)(pp * 2 + slot) * b + c) * len;
-    const int pos = slot == 0 ? me : 2 * P - 1 - me;
-    const int M = 2 * P - 1;
-    const int blk = pos == 0 ? 0 : 1 + ((pos - 1 - rnd) % M + M) % M;
-    return gm + ((size_t)blk * b + c) * len;
+    if constexpr (!kGlobal) {
+      return base + ((size_t)(pp * 2 + slot) * b + c) * len;
+    } else {
+      const int pos = slot == 0 ? me : 2 * P - 1 - me;
+      const int M = 2 * P - 1;
+      const int blk = pos == 0 ? 0 : 1 + ((pos - 1 - rnd) % M + M) % M;
+      return base + ((size_t)blk * b + c) * len;
+    }
   }
 };
 
@@ -179,8 +184,8 @@ struct ColStore {
 // sweep rotates no pair (or max_sweeps); kOp 1: max_sweeps orthonormalisation
 // sweeps.  Every CTA of the cluster calls it (non-members only keep the
 // cluster barriers in step).  Returns the sweeps run.
-template <typename T, int kOp>
-__device__ int cluster_sweeps(const ClusterGeom& g, const ColStore<T>& cs, int& cur, int max_sweeps, T tol, T floor,
+template <typename T, int kOp, bool kGlobal>
+__device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColStore<T, kGlobal>& cs, int& cur, int max_sweeps, T tol, T floor,
                               T tiny, T tau2, bool& converged, const cg::cluster_group& cluster, int* s_flag_in,
                               int* s_any) {
   using C = cplx<T>;
@@ -256,7 +261,7 @@ __device__ int cluster_sweeps(const ClusterGeom& g, const ColStore<T>& cs, int& 
         __syncthreads();
       }
       if (g.P == 1) continue;  // a single CTA keeps its blocks (and needs no cluster barrier)
-      if (cs.sm) {
+      if constexpr (!kGlobal) {
         // hand the blocks on: position pos -> pos + 1 (pos >= 1), 2P-1 -> 1
         const int nxt = cur ^ 1;
         const size_t units = (size_t)g.b * g.len * sizeof(C) / sizeof(uint4);
@@ -298,6 +303,11 @@ __device__ int cluster_sweeps(const ClusterGeom& g, const ColStore<T>& cs, int& 
   return sweep;
 }
 
+// Threads per CTA of the cluster SVD: FP64 columns need more registers per
+// thread (the cached column alone is 64), so FP64 CTAs stop at 8 warps and a
+// warp takes several pairs in turn when a block has more than 8 columns.
+template <typename S> constexpr int kClusterMaxThreads = sizeof(S) == 8 ? 256 : 512;
+
 template <typename S>
 struct ClusterSvdSmem {
   // layout of the dynamic shared memory (offsets in bytes); len = m + n
@@ -322,58 +332,30 @@ __host__ __device__ inline size_t cluster_svd_workspace(size_t mcap, size_t ncap
   return s_bytes == 8 ? e + (e + 1) / 2 : e;
 }
 
-template <typename S, typename R>
-__global__ void __launch_bounds__(512, 1)
-    svd_cluster_kernel(const cplx<R>* __restrict__ Cm, const double* __restrict__ lam_l, int* __restrict__ chi, int q,
-                       SvdParams p, cplx<R>* __restrict__ Bnext, double* __restrict__ lam_next,
-                       DevReport* __restrict__ rep, cplx<S>* __restrict__ gbuf, unsigned smem_bytes) {
+// Everything after the geometry: the column layout (shared or global) is a
+// compile-time choice so that shared-memory accesses compile as such.
+template <typename S, typename R, bool kGlobal>
+__device__ __forceinline__ void svd_cluster_body(const ClusterGeom& g, const cg::cluster_group& cluster,
+                                                 const cplx<R>* __restrict__ Cm, const double* __restrict__ lam_l,
+                                                 int* __restrict__ chi, int q, const SvdParams& p,
+                                                 cplx<R>* __restrict__ Bnext, double* __restrict__ lam_next,
+                                                 DevReport* __restrict__ rep, cplx<S>* __restrict__ gbuf,
+                                                 unsigned char* smem, int* s_flag_in, double* s_fro, int& s_k,
+                                                 double& s_nrm, int* s_any, long long t_start) {
   using C = cplx<S>;
-  cg::cluster_group cluster = cg::this_cluster();
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_flag_in[16];
-  __shared__ double s_fro[16];
-  __shared__ int s_k;
-  __shared__ double s_nrm;
-  __shared__ int s_any;
-
-  const long long t_start = clock64();
   long long t_load = 0, t_lo = 0, t_fix = 0;
-  ClusterGeom g;
-  g.Pl = (int)cluster.num_blocks();  // CTAs launched (sized for the bond capacities)
-  g.me = (int)cluster.block_rank();
-  const int chi_l = chi[q], chi_r = chi[q + 2];
-  g.m = 2 * chi_l;      // rows of A
-  g.ncols = 2 * chi_r;  // columns of A = rows of V
-  g.len = g.m + g.ncols;
-  g.nw = (int)(blockDim.x >> 5);
-  g.nt = blockDim.x;
-  g.wl = threadIdx.x & 31;
-  g.wp = threadIdx.x >> 5;
   const bool mixed = sizeof(S) == 8 && sizeof(R) == 4 && p.mixed;
-  // CTAs that take part, from the actual bond dimensions: complex64 pair
-  // steps are latency-bound, so as few CTAs as the warps allow (fewer rounds
-  // and cluster barriers); FP64 ones are bound by the FP64 units, so one pair
-  // per warp on as many CTAs as there are.  The others (rank >= P) only keep
-  // the cluster barriers in step.
-  const int per = sizeof(S) == 8 ? 1 : g.nw;
-  g.P = min(g.Pl, max(1, (g.ncols + 2 * per - 1) / (2 * per)));
-  g.member = g.me < g.P;
-  g.b = (g.ncols + 2 * g.P - 1) / (2 * g.P);  // a warp takes pairs w, w + nw, ...
-  g.ncols_pad = 2 * g.P * g.b;
   const int m = g.m, ncols = g.ncols, len = g.len, b = g.b, P = g.P, me = g.me, nt = g.nt;
-
-  // Shared memory when the stacked columns fit the launch's allocation, else the global workspace.
-  const bool in_smem = gbuf == nullptr || ClusterSvdSmem<S>(b, len, g.ncols_pad, nt).total <= smem_bytes;
-  const ClusterSvdSmem<S> L(b, in_smem ? len : 0, g.ncols_pad, nt);
+  const ClusterSvdSmem<S> L(b, kGlobal ? 0 : len, g.ncols_pad, nt);
   double* sig = reinterpret_cast<double*>(smem + L.sig);
   int* rnk = reinterpret_cast<int*>(smem + L.rank);
-  const ColStore<S> cs{in_smem ? reinterpret_cast<C*>(smem + L.buf) : nullptr, gbuf, b, len, P, me};
+  const ColStore<S, kGlobal> cs{kGlobal ? gbuf : reinterpret_cast<C*>(smem + L.buf), b, len, P, me};
   // FP32 columns of the mixed form: in shared memory both FP32 ping-pong
   // buffers fit in the first S ping-pong buffer; in global memory they follow
   // the S blocks.
-  const ColStore<float> cs32{in_smem ? reinterpret_cast<cplx<float>*>(smem + L.buf) : nullptr,
-                             in_smem ? nullptr : reinterpret_cast<cplx<float>*>(gbuf + (size_t)g.ncols_pad * len), b,
-                             len, P, me};
+  const ColStore<float, kGlobal> cs32{kGlobal ? reinterpret_cast<cplx<float>*>(gbuf + (size_t)g.ncols_pad * len)
+                                               : reinterpret_cast<cplx<float>*>(smem + L.buf),
+                                      b, len, P, me};
 
   // ---- load: position pos holds the initial block pos (columns pos*b ..)
   for (int slot = 0; slot < 2 && g.member; ++slot) {
@@ -434,13 +416,13 @@ __global__ void __launch_bounds__(512, 1)
     const float u32 = 5.9604645e-08f;
     int cur32 = 0;
     bool conv32 = false;
-    used32 = cluster_sweeps<float, 0>(g, cs32, cur32, p.max_sweeps, float(tol_scale) * u32,
+    used32 = cluster_sweeps<float, 0, kGlobal>(g, cs32, cur32, p.max_sweeps, float(tol_scale) * u32,
                                       float(16.0 * double(u32) * double(u32) * fro2), 1e-35f, float(tau2), conv32,
-                                      cluster, s_flag_in, &s_any);
+                                      cluster, s_flag_in, s_any);
     used = used32;
     t_lo = clock64();
     // FP64 columns: V promoted (A follows from the theta below)
-    cur = in_smem ? 1 : 0;
+    cur = kGlobal ? 0 : 1;
     for (int slot = 0; slot < 2 && g.member; ++slot)
       for (size_t t = threadIdx.x; t < (size_t)b * ncols; t += nt) {
         const int c = (int)(t / ncols), r = m + (int)(t % ncols);
@@ -451,7 +433,7 @@ __global__ void __launch_bounds__(512, 1)
     // overwrite them (in shared memory they share a buffer with FP64 ones)
     cluster.sync();
     bool dummy;
-    cluster_sweeps<S, 1>(g, cs, cur, 1, S(0), S(0), S(0), S(0), dummy, cluster, s_flag_in, &s_any);
+    cluster_sweeps<S, 1, kGlobal>(g, cs, cur, 1, S(0), S(0), S(0), S(0), dummy, cluster, s_flag_in, s_any);
     // the diagonal of the first-order step: |v|^2 -> 1
     for (int c = g.wp; g.member && c < 2 * b; c += g.nw) {
       C* v = cs.col(cur, c / b, c % b, 0);
@@ -485,8 +467,8 @@ __global__ void __launch_bounds__(512, 1)
   const S tol = p.tol > 0 ? S(p.tol) : S(tol_scale) * eps_u;
   const S floor = S(16.0 * double(eps_u) * double(eps_u) * fro2);
   const S tiny = sizeof(S) == 8 ? S(1e-290) : S(1e-35f);
-  used += cluster_sweeps<S, 0>(g, cs, cur, p.max_sweeps, tol, floor, tiny, S(tau2), converged, cluster, s_flag_in,
-                               &s_any);
+  used += cluster_sweeps<S, 0, kGlobal>(g, cs, cur, p.max_sweeps, tol, floor, tiny, S(tau2), converged, cluster, s_flag_in,
+                               s_any);
   const int sweep = used;
 
   // ---- singular values: norms of the A parts, shared with every CTA
@@ -579,6 +561,55 @@ __global__ void __launch_bounds__(512, 1)
     for (int r = lane; r < ncols; r += 32) Bnext[(size_t)a * ncols + r] = ccast<cplx<R>>(cconj(v[r]));
   }
   cluster.sync();  // no CTA leaves while its shared memory may still be read
+}
+
+
+template <typename S, typename R>
+__global__ void __launch_bounds__(kClusterMaxThreads<S>, 1)
+    svd_cluster_kernel(const cplx<R>* __restrict__ Cm, const double* __restrict__ lam_l, int* __restrict__ chi, int q,
+                       SvdParams p, cplx<R>* __restrict__ Bnext, double* __restrict__ lam_next,
+                       DevReport* __restrict__ rep, cplx<S>* __restrict__ gbuf, unsigned smem_bytes) {
+  using C = cplx<S>;
+  cg::cluster_group cluster = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_flag_in[16];
+  __shared__ double s_fro[16];
+  __shared__ int s_k;
+  __shared__ double s_nrm;
+  __shared__ int s_any;
+
+  const long long t_start = clock64();
+  ClusterGeom g;
+  g.Pl = (int)cluster.num_blocks();  // CTAs launched (sized for the bond capacities)
+  g.me = (int)cluster.block_rank();
+  const int chi_l = chi[q], chi_r = chi[q + 2];
+  g.m = 2 * chi_l;      // rows of A
+  g.ncols = 2 * chi_r;  // columns of A = rows of V
+  g.len = g.m + g.ncols;
+  g.nw = (int)(blockDim.x >> 5);
+  g.nt = blockDim.x;
+  g.wl = threadIdx.x & 31;
+  g.wp = threadIdx.x >> 5;
+  // CTAs that take part, from the actual bond dimensions: complex64 pair
+  // steps are latency-bound, so as few CTAs as the warps allow (fewer rounds
+  // and cluster barriers); FP64 ones are bound by the FP64 units, so one pair
+  // per warp on as many CTAs as there are.  The others (rank >= P) only keep
+  // the cluster barriers in step.
+  const int per = sizeof(S) == 8 ? 1 : g.nw;
+  g.P = min(g.Pl, max(1, (g.ncols + 2 * per - 1) / (2 * per)));
+  g.member = g.me < g.P;
+  g.b = (g.ncols + 2 * g.P - 1) / (2 * g.P);  // a warp takes pairs w, w + nw, ...
+  g.ncols_pad = 2 * g.P * g.b;
+
+  // Shared memory when the stacked columns fit the launch's allocation, else the global workspace.
+  const bool in_smem =
+      gbuf == nullptr || ClusterSvdSmem<S>(g.b, g.len, g.ncols_pad, g.nt).total <= smem_bytes;
+  if (in_smem)
+    svd_cluster_body<S, R, false>(g, cluster, Cm, lam_l, chi, q, p, Bnext, lam_next, rep, gbuf, smem, s_flag_in,
+                                  s_fro, s_k, s_nrm, &s_any, t_start);
+  else
+    svd_cluster_body<S, R, true>(g, cluster, Cm, lam_l, chi, q, p, Bnext, lam_next, rep, gbuf, smem, s_flag_in,
+                                 s_fro, s_k, s_nrm, &s_any, t_start);
 }
 
 }  // namespace mpsv
