@@ -214,6 +214,33 @@ mps_status mps_energy_async(mps_state* st, const mps_ham* h, double* d_energy_ou
 /* Per-term expectation values <P_k> (host array of n_terms doubles). */
 mps_status mps_expectations(mps_state* st, const mps_ham* h, double* values_out);
 
+/* Linear observables of one string set: the reduced density matrices of the
+ * paper's Methods, "The DMET method" (1-RDM <a+_p a_q>, 2-RDM
+ * <a+_p a+_q a_r a_s>, from which the fragment energy and electron count
+ * follow).  Under the Jordan-Wigner map every RDM element is a complex
+ * combination of Pauli strings, so all of them follow from the per-string
+ * values <P_j> (Eq. expec2, environments shared through the trie of the
+ * string set):
+ *   values[r] = sum_{e = row_ptr[r]}^{row_ptr[r+1]-1} weights[e] <P_{cols[e]}>.
+ * `strings` is a Hamiltonian handle whose terms are the strings P_j (its
+ * coefficients are not used); it must outlive the observables handle, which
+ * lives in its context.  row_ptr: n_rows + 1 int64, row_ptr[0] = 0,
+ * non-decreasing; cols: row_ptr[n_rows] int32 in [0, n_terms); weights:
+ * 2 * row_ptr[n_rows] doubles (re, im), finite.  All host arrays, copied
+ * during the call.  MPS_EINVAL for NULL or inconsistent arguments (no handle
+ * is created; *out = NULL), MPS_ENOMEM / MPS_ECUDA from the upload. */
+typedef struct mps_obs mps_obs;
+mps_status mps_observables_create(const mps_ham* strings, size_t n_rows, const int64_t* row_ptr,
+                                  const int32_t* cols, const double* weights, mps_obs** out);
+/* Evaluate every row for the state's current MPS: values_out is a host array
+ * of 2 * n_rows doubles (re, im).  The per-string values come from the
+ * energy kernels; the row sums run on the device in FP64 in a fixed order
+ * (one launch).  The state keeps an output buffer of n_rows entries between
+ * calls.  Synchronises the state's stream; MPS_EINVAL if the string set has
+ * another qubit count or device than the state. */
+mps_status mps_observables_eval(mps_state* st, const mps_obs* obs, double* values_out);
+void mps_observables_destroy(mps_obs* obs);
+
 /* Bond dimensions chi_0..chi_n (host array of n+1 int32). */
 mps_status mps_bond_dims(mps_state* st, int32_t* chi_out);
 /* Host copy of the state: tensors_out receives every B_n (row-major

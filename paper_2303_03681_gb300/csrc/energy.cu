@@ -664,3 +664,133 @@ mps_status vqe_eval_batch_async(const vqe_request* reqs, size_t n, double* d_ene
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Linear observables over one string set: reduced density matrices
+// ---------------------------------------------------------------------------
+
+struct mps_obs {
+  mps_ctx* ctx = nullptr;  // the string set's context (owns the arrays below)
+  const mps_ham* strings = nullptr;
+  long long n_rows = 0, nnz = 0;
+  long long* d_row_ptr = nullptr;
+  int* d_cols = nullptr;
+  double2* d_w = nullptr;
+};
+
+static void destroy_obs(mps_obs* o) {
+  if (!o) return;
+  mps_ctx* c = o->ctx;
+  DeviceGuard guard(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (void* p : {(void*)o->d_row_ptr, (void*)o->d_cols, (void*)o->d_w}) dev_free(c, p);
+  delete o;
+}
+
+extern "C" {
+
+mps_status mps_observables_create(const mps_ham* strings, size_t n_rows, const int64_t* row_ptr,
+                                  const int32_t* cols, const double* weights, mps_obs** out) {
+  if (!strings || !out || !row_ptr) {
+    set_error("mps_observables_create: NULL argument");
+    return MPS_EINVAL;
+  }
+  *out = nullptr;
+  if (n_rows > (size_t)INT32_MAX * 8) {
+    set_error("mps_observables_create: n_rows = %zu is too large", n_rows);
+    return MPS_EINVAL;
+  }
+  if (row_ptr[0] != 0) {
+    set_error("mps_observables_create: row_ptr[0] = %lld, must be 0", (long long)row_ptr[0]);
+    return MPS_EINVAL;
+  }
+  for (size_t r = 0; r < n_rows; ++r)
+    if (row_ptr[r + 1] < row_ptr[r]) {
+      set_error("mps_observables_create: row_ptr decreases at row %zu", r);
+      return MPS_EINVAL;
+    }
+  const long long nnz = row_ptr[n_rows];
+  if (nnz > 0 && (!cols || !weights)) {
+    set_error("mps_observables_create: NULL cols or weights for %lld entries", nnz);
+    return MPS_EINVAL;
+  }
+  for (long long e = 0; e < nnz; ++e) {
+    if (cols[e] < 0 || cols[e] >= strings->n_terms) {
+      set_error("mps_observables_create: cols[%lld] = %d is not a string index (0..%lld)", e, cols[e],
+                strings->n_terms - 1);
+      return MPS_EINVAL;
+    }
+    if (!std::isfinite(weights[2 * e]) || !std::isfinite(weights[2 * e + 1])) {
+      set_error("mps_observables_create: weight %lld is not finite", e);
+      return MPS_EINVAL;
+    }
+  }
+  mps_ctx* c = strings->ctx;
+  DeviceGuard guard(c->device);
+  auto* o = new mps_obs();
+  o->ctx = c;
+  o->strings = strings;
+  o->n_rows = (long long)n_rows;
+  o->nnz = nnz;
+  mps_status rc = dev_alloc(c, (void**)&o->d_row_ptr, (n_rows + 1) * sizeof(long long));
+  if (rc == MPS_OK) rc = dev_alloc(c, (void**)&o->d_cols, (size_t)nnz * sizeof(int));
+  if (rc == MPS_OK) rc = dev_alloc(c, (void**)&o->d_w, (size_t)nnz * sizeof(double2));
+  if (rc == MPS_OK) {
+    cudaError_t e = cudaMemcpy(o->d_row_ptr, row_ptr, (n_rows + 1) * sizeof(long long), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nnz)
+      e = cudaMemcpy(o->d_cols, cols, (size_t)nnz * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nnz)
+      e = cudaMemcpy(o->d_w, weights, (size_t)nnz * sizeof(double2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) rc = cuda_fail(e, "mps_observables_create: upload");
+  }
+  if (rc != MPS_OK) {
+    destroy_obs(o);
+    return rc;
+  }
+  *out = o;
+  return MPS_OK;
+}
+
+mps_status mps_observables_eval(mps_state* st, const mps_obs* o, double* values_out) {
+  if (!st || !o || (!values_out && o->n_rows)) {
+    set_error("mps_observables_eval: NULL argument");
+    return MPS_EINVAL;
+  }
+  if (o->ctx->device != st->ctx->device) {
+    set_error("mps_observables_eval: observables on device %d, state on device %d", o->ctx->device,
+              st->ctx->device);
+    return MPS_EINVAL;
+  }
+  DeviceGuard guard(st->ctx->device);
+  mps_status rc = ham_energy_async(st, const_cast<mps_ham*>(o->strings), nullptr);
+  if (rc != MPS_OK) return rc;
+  if ((size_t)o->n_rows > st->obs_cap || !st->d_obs) {
+    MPSV_CUDA(cudaStreamSynchronize(st->ctx->stream));
+    dev_free(st->ctx, st->d_obs);
+    st->d_obs = nullptr;
+    st->obs_cap = 0;
+    rc = dev_alloc(st->ctx, (void**)&st->d_obs, std::max<size_t>(16, (size_t)o->n_rows * sizeof(double2)));
+    if (rc != MPS_OK) return rc;
+    st->obs_cap = (size_t)o->n_rows;
+  }
+  cudaStream_t s = st->ctx->stream;
+  if (o->n_rows) {
+    {
+      KernelScope k(st->ctx, MPS_K_REDUCE);
+      const long long blocks = (o->n_rows + 7) / 8;  // 8 warps (rows) per 256-thread block
+      observables_kernel<<<(unsigned)blocks, 256, 0, s>>>(st->d_vals, o->d_row_ptr, o->d_cols, o->d_w, o->n_rows,
+                                                           st->d_obs);
+    }
+    MPSV_CUDA(cudaGetLastError());
+    MPSV_CUDA(cudaMemcpyAsync(values_out, st->d_obs, (size_t)o->n_rows * sizeof(double2), cudaMemcpyDeviceToHost,
+                              s));
+  }
+  int tc_flag = 0;
+  MPSV_CUDA(queue_tc_flag(st, &tc_flag));
+  MPSV_CUDA(cudaStreamSynchronize(s));
+  return tc_flag_status(tc_flag);
+}
+
+void mps_observables_destroy(mps_obs* o) { destroy_obs(o); }
+
+}  // extern "C"

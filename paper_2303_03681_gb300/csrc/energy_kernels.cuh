@@ -222,6 +222,31 @@ static __global__ void fill_kernel(double* __restrict__ p, long long n, double v
   if (t < n) p[t] = v;
 }
 
+// Linear observables of the per-string values (reduced density matrices):
+// out[r] = sum_{e in [row_ptr[r], row_ptr[r+1])} w[e] * vals[cols[e]], complex
+// weights, FP64.  One warp per row; lane l takes the entries l, l + 32, ...
+// and the lanes are summed in a fixed tree, so the result does not depend on
+// the launch.  blockDim.x must be a multiple of 32 (whole warps leave
+// together, so the shuffles see full warps).
+static __global__ void observables_kernel(const double* __restrict__ vals, const long long* __restrict__ row_ptr,
+                                          const int* __restrict__ cols, const double2* __restrict__ w,
+                                          long long n_rows, double2* __restrict__ out) {
+  const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (r >= n_rows) return;
+  double re = 0.0, im = 0.0;
+  const long long end = row_ptr[r + 1];
+  for (long long e = row_ptr[r] + lane; e < end; e += 32) {
+    const double v = vals[cols[e]];
+    const double2 c = w[e];
+    re = fma(c.x, v, re);
+    im = fma(c.y, v, im);
+  }
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if (lane == 0) out[r] = make_double2(re, im);
+}
+
 // ---------------------------------------------------------------------------
 // tensor-core forms (complex64 states): the same products as env_m_kernel and
 // env_child_kernel, as problems of tc::cgemm_kernel

@@ -135,6 +135,9 @@ struct mps_state {
   size_t vals_cap = 0;
   double* d_energy = nullptr;
   mpsv::CircuitGraph* graph = nullptr;  // last captured circuit (graph replay)
+  // linear observables over per-string expectations (mps_observables_eval)
+  double2* d_obs = nullptr;
+  size_t obs_cap = 0;
 };
 
 struct mps_circuit {

@@ -520,7 +520,7 @@ static void destroy_state(mps_state* st) {
   for (void* p : {st->d_B, (void*)st->d_lam, (void*)st->d_chi, (void*)st->d_site_off, (void*)st->d_lam_off,
                   (void*)st->d_bits, (void*)st->d_rep, st->d_C, st->d_A, st->d_V, (void*)st->d_gates,
                   (void*)st->d_bound, (void*)st->d_theta, st->d_L[0], st->d_L[1], st->d_M, (void*)st->d_vals,
-                  (void*)st->d_energy})
+                  (void*)st->d_energy, (void*)st->d_obs})
     dev_free(c, p);
   delete st;
 }

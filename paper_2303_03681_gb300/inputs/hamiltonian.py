@@ -265,6 +265,42 @@ def jw_molecular_hamiltonian(h: np.ndarray, g: np.ndarray, constant: float = 0.0
     return PauliSum(n_so, ops, coeffs)
 
 
+def fermion_monomial_map(n_so: int, ops, tol: float = 1e-14):
+    """JW-map K fermionic monomials separately, sharing one set of strings.
+
+    ``ops`` lists the operators left to right as (idx (K,), dagger); monomial
+    k is prod_m op_m[k].  Returns (strings, row_ptr, cols, weights): the
+    distinct Pauli strings (T, n_so) uint8 and a CSR map with
+    monomial k = sum_{e in row_ptr[k]:row_ptr[k+1]} weights[e] * strings[cols[e]]
+    (complex weights, entries of one row in increasing column order).
+    """
+    tables = _bit_tables(n_so)
+    idx0 = np.asarray(ops[0][0])
+    K = int(idx0.shape[0])
+    if K == 0:
+        return (np.zeros((0, n_so), np.uint8), np.zeros(1, np.int64), np.zeros(0, np.int32),
+                np.zeros(0, complex))
+    factors = [_ladder_factor(np.asarray(idx), dag, tables) for idx, dag in ops]
+    x, z, coef = _expand_products(factors, np.ones(K, dtype=complex))
+    coef = _to_standard(x, z, coef)
+    mono = np.tile(np.arange(K, dtype=np.int64), 1 << len(ops))  # _expand_products stacks combination-major
+    rows = np.ascontiguousarray(np.concatenate([x, z], axis=1), dtype=np.uint64)
+    void = rows.view(np.dtype((np.void, rows.dtype.itemsize * rows.shape[1]))).ravel()
+    uniq, first, inv = np.unique(void, return_index=True, return_inverse=True)
+    T = int(uniq.shape[0])
+    key = mono * T + inv.reshape(-1)
+    ukey, kinv = np.unique(key, return_inverse=True)
+    w = (np.bincount(kinv, weights=coef.real, minlength=ukey.shape[0])
+         + 1j * np.bincount(kinv, weights=coef.imag, minlength=ukey.shape[0]))
+    keep = np.abs(w) > tol
+    ukey, w = ukey[keep], w[keep]
+    row_of, col_of = ukey // T, ukey % T
+    used, cols = np.unique(col_of, return_inverse=True)
+    strings = _symplectic_to_ops(rows[first[used]], n_so)
+    row_ptr = np.searchsorted(row_of, np.arange(K + 1)).astype(np.int64)
+    return strings, row_ptr, cols.astype(np.int32), w
+
+
 def _chunked(terms, chunk):
     for weight, ops in terms:
         k = weight.shape[0]

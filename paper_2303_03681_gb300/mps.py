@@ -86,6 +86,9 @@ def _load():
         "mps_energy": ([P, P, ctypes.POINTER(D), ctypes.POINTER(D)], ctypes.c_int),
         "mps_energy_async": ([P, P, P], ctypes.c_int),
         "mps_expectations": ([P, P, P], ctypes.c_int),
+        "mps_observables_create": ([P, SZ, P, P, P, PP], ctypes.c_int),
+        "mps_observables_eval": ([P, P, P], ctypes.c_int),
+        "mps_observables_destroy": ([P], None),
         "mps_bond_dims": ([P, P], ctypes.c_int),
         "mps_export": ([P, P, SZ, P, SZ], ctypes.c_int),
         "mps_get_report": ([P, ctypes.POINTER(Report)], ctypes.c_int),
@@ -303,6 +306,28 @@ class Hamiltonian(_Child):
         return {"n_terms": a.value, "n_nodes": b.value, "max_level_nodes": c.value}
 
 
+class Observables(_Child):
+    """Rows of complex weights over the strings of a Hamiltonian handle
+    (mps_observables_create): row r is sum_e weights[e] <P_{cols[e]}> over
+    e in row_ptr[r]:row_ptr[r+1]."""
+
+    _destroy = staticmethod(lambda h: _lib.mps_observables_destroy(h))
+
+    def __init__(self, strings: Hamiltonian, row_ptr, cols, weights):
+        self._adopt(strings.ctx)
+        self.strings = strings  # the string set must outlive this handle
+        rp = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        c = np.ascontiguousarray(cols, dtype=np.int32)
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.complex128)).view(np.float64)
+        if rp.ndim != 1 or rp.shape[0] < 1:
+            raise ValueError("row_ptr needs n_rows + 1 entries")
+        self.n_rows = int(rp.shape[0] - 1)
+        h = ctypes.c_void_p()
+        _check(_lib.mps_observables_create(strings.handle, self.n_rows, _ptr(rp), _ptr(c), _ptr(w),
+                                           ctypes.byref(h)))
+        self.handle = h
+
+
 class Circuit(_Child):
     _destroy = staticmethod(lambda h: _lib.mps_circuit_destroy(h))
 
@@ -368,6 +393,12 @@ class State(_Child):
         out = np.zeros(ham.n_terms)
         _check(_lib.mps_expectations(self.handle, ham.handle, _ptr(out)))
         return out
+
+    def observables(self, obs: Observables) -> np.ndarray:
+        """Complex values of every row of ``obs`` for the current state."""
+        out = np.zeros(2 * obs.n_rows)
+        _check(_lib.mps_observables_eval(self.handle, obs.handle, _ptr(out)))
+        return out.view(np.complex128)
 
     def bond_dims(self) -> np.ndarray:
         out = np.zeros(self.n + 1, dtype=np.int32)
