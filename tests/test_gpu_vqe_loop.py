@@ -34,15 +34,20 @@ def test_batched_loop_reaches_h2_full_ci():
 
 
 def test_batched_loop_follows_the_oracle_loop():
-    """Same optimiser, GPU energies vs dense-statevector energies: the
-    trajectories agree to rounding and stay above the exact sector energy."""
+    """Same optimiser, GPU energies vs dense-statevector energies: the energy
+    trajectories agree to rounding and stay above the exact sector energy.
+
+    The angles are not unique: moving two coupled single-excitation angles
+    by pi each can leave E unchanged, so a one-angle model can have two equal
+    minima and rounding picks one.  The test therefore compares the energies
+    and checks the GPU's angles by the oracle's energy at them."""
     ham, tmpl, bits = small_molecule(3, 2, 81)
     gpu = BatchedEnergy(tmpl, ham, bits, slots=4, chi_max=8, precision="fp64")
     ref = DenseEnergy(tmpl, ham, bits)
     a = sequential_minimize(gpu, np.zeros(tmpl.n_params), max_sweeps=4, tol=0.0)
     b = sequential_minimize(ref, np.zeros(tmpl.n_params), max_sweeps=4, tol=0.0)
     assert np.max(np.abs(np.array(a.history) - np.array(b.history))) <= 1e-9
-    assert np.max(np.abs(a.theta - b.theta)) <= 1e-6
+    assert abs(ref(a.theta[None])[0] - a.energy) <= 1e-10
     assert a.energy >= sector_ground_energy(ham, 2) - 1e-10
     assert a.n_evals == b.n_evals and a.n_batches == b.n_batches
     gpu.close()
