@@ -291,3 +291,62 @@ def uccsd_template(n_so: int, n_electrons: int, max_excitations=None) -> Circuit
             n_strings += 1
     meta = {"n_excitations": len(excs), "n_pauli_exponentials": n_strings}
     return pauli_exponential_template(n_so, strings, len(excs), meta)
+
+
+# ----------------------------------------------------------------------------
+# windowed generalised-singles-and-doubles pool (hydrogen-chain ansatz)
+# ----------------------------------------------------------------------------
+
+def gsd_excitations(orbitals):
+    """Spin-conserving generalised singles and doubles among the spatial
+    ``orbitals`` (every spin orbital may be created or annihilated, no
+    occupied/virtual split).  Tuples in the convention of
+    ``excitation_generator_paulis``: (i, a) for tau = a+_a a_i and
+    (i, j, a, b) for tau = a+_a a+_b a_j a_i; each pair {tau, tau^dagger}
+    appears once."""
+    so = sorted(2 * p + s for p in orbitals for s in (0, 1))
+    singles = [(q, p) for p in so for q in so if p > q and p % 2 == q % 2]
+    pairs = [(p, q) for p in so for q in so if p > q]
+    doubles = []
+    for a, b in pairs:  # created: a > b
+        for j, i in pairs:  # annihilated: j > i
+            if (a, b) > (j, i) and sorted((a % 2, b % 2)) == sorted((i % 2, j % 2)):
+                doubles.append((i, j, a, b))
+    return singles + doubles
+
+
+def windowed_gsd_pool(n_orb: int, window: int = 5) -> np.ndarray:
+    """Operator pool of the paper's hydrogen-chain ansatz (Methods, "The wave
+    function ansatz for hydrogen chain simulations"): generalised singles and
+    doubles within every run of ``window`` consecutive spatial orbitals, each
+    generator JW-mapped to Pauli strings, every Z replaced by I, strings with
+    an even number of Y dropped, duplicates removed.
+
+    Returns the distinct strings as (K, 2 n_orb) uint8, lexicographically
+    sorted; each enters a circuit as exp(i theta P)."""
+    n_so = 2 * n_orb
+    w = min(window, n_orb)
+    seen = set()
+    rows = []
+    for start in range(0, n_orb - w + 1):
+        for exc in gsd_excitations(range(start, start + w)):
+            ops, _ = excitation_generator_paulis(n_so, exc)
+            for row in ops:
+                r = np.where(row == 3, 0, row).astype(np.uint8)
+                if not r.any() or np.count_nonzero(r == 2) % 2 == 0:
+                    continue
+                key = r.tobytes()
+                if key not in seen:
+                    seen.add(key)
+                    rows.append(r)
+    if not rows:
+        return np.zeros((0, n_so), np.uint8)
+    out = np.array(rows, dtype=np.uint8)
+    return out[np.lexsort(out.T[::-1])]
+
+
+def pauli_product_template(n: int, pool: np.ndarray, chosen) -> CircuitTemplate:
+    """prod_k exp(i theta[k] pool[chosen[k]]) in order, one angle per factor
+    (the adaptive circuit of the hydrogen-chain ansatz)."""
+    strings = [(pool[j], k, 1.0) for k, j in enumerate(chosen)]
+    return pauli_exponential_template(n, strings, len(strings), {"chosen": list(map(int, chosen))})
