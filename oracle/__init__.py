@@ -16,12 +16,17 @@ Contents (each function cites the passage of arXiv:2303.03681 it follows):
 * ``dense``       - brute-force dense statevector simulation (small n).
 * ``fock``        - occupation-number-basis Hamiltonian, dense JW ladder
                     operators and the closed-form Hartree-Fock energy.
+* ``rdm``         - 1- and 2-RDMs of a statevector by their definition
+                    (ladder operators on occupation bit strings), their
+                    spin-summed forms and the RDM energy (Methods, "The DMET
+                    method").
 
 Pins (tests/test_oracle_*.py, all ``-m "not gpu"``): dense statevector at
 uncapped bond dimension, the Hartree-Fock determinant energy, the
 occupation-basis Hamiltonian, LAPACK singular values, canonical-form and
 norm invariants, product-state expectation values, expm of each UCCSD
-generator.  Parity unpinned: truncated evolutions (bond dimension capped
+generator, the Hartree-Fock RDMs, trace and partial-trace identities of the
+RDMs and the RDM energy against the Pauli-sum energy.  Parity unpinned: truncated evolutions (bond dimension capped
 below the exact rank) have no closed form; there the oracle is checked only
 through its invariants (canonical form, unit norm, discarded-weight bound).
 """
