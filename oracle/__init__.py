@@ -21,12 +21,15 @@ Contents (each function cites the passage of arXiv:2303.03681 it follows):
                     spin-summed forms and the RDM energy (Methods, "The DMET
                     method").
 
-Pins (tests/test_oracle_*.py, all ``-m "not gpu"``): dense statevector at
-uncapped bond dimension, the Hartree-Fock determinant energy, the
-occupation-basis Hamiltonian, LAPACK singular values, canonical-form and
-norm invariants, product-state expectation values, expm of each UCCSD
-generator, the Hartree-Fock RDMs, trace and partial-trace identities of the
-RDMs and the RDM energy against the Pauli-sum energy.  Parity unpinned: truncated evolutions (bond dimension capped
-below the exact rank) have no closed form; there the oracle is checked only
-through its invariants (canonical form, unit norm, discarded-weight bound).
+Pins (tests/test_oracle_*.py, tests/test_rdm.py, all ``-m "not gpu"``):
+dense statevector at uncapped bond dimension, the Hartree-Fock determinant
+energy, the occupation-basis Hamiltonian, LAPACK singular values,
+canonical-form and norm invariants, product-state expectation values, expm
+of each UCCSD generator, the Hartree-Fock RDMs, trace and partial-trace
+identities of the RDMs, and the RDM energy against the Pauli-sum energy.
+Truncation (the rank rule and the renormalisation) is pinned by the dense
+Schmidt truncation: one truncated gate on an exact state gives the best
+rank-k approximation across that cut (Eckart-Young).  A sequence of
+truncations has no closed form; there the oracle is checked through its
+invariants (canonical form, unit norm, 1 - F <= 2 x discarded weight).
 """

@@ -116,6 +116,35 @@ def test_truncated_run_invariants():
     assert abs(om.energy(exact, ham) - e_exact) <= 1e-10
 
 
+@pytest.mark.parametrize("chi_cap,eps_rel", [(6, 0.0), (64, 0.05)])
+def test_single_truncation_is_the_dense_schmidt_truncation(chi_cap, eps_rel):
+    """On an exact canonical state the SVD of C~ (Eq. svdtildeC) is the Schmidt
+    decomposition across the bond between sites q and q+1, so one truncated
+    gate must give the best rank-k approximation of the dense state across
+    that cut (Eckart-Young), renormalised: the same state, lam = the k
+    largest dense singular values over their norm, and discarded weight
+    1 - sum(kept s^2) / sum(s^2).  k follows the truncation rule (chi cap or
+    relative threshold)."""
+    from paper_2303_03681_gb300.inputs.circuits import haar_su4
+
+    n, q = 10, 4
+    rng = make_rng(MASTER_SEED + 20)
+    mps = om.run_circuit(n, None, brickwork_circuit(n, 6, rng), chi_max=64)
+    u = haar_su4(rng)
+    psi = od.apply_gate(om.to_statevector(mps), n, q, 2, u)
+    U, s, Vh = np.linalg.svd(psi.reshape(1 << (q + 1), -1), full_matrices=False)
+    k = om.truncation_rank(s, chi_cap, eps_rel)
+    assert np.count_nonzero(s > 1e-12) > k  # the cut really truncates
+    om.apply_2q(mps, q, u, chi_max=chi_cap, eps_rel=eps_rel)
+    best = (U[:, :k] * s[:k]) @ Vh[:k]
+    best = best.reshape(-1) / np.linalg.norm(s[:k])
+    got = om.to_statevector(mps)
+    assert mps.B[q].shape[2] == k
+    assert abs(abs(np.vdot(best, got)) ** 2 - 1.0) <= 1e-12
+    assert np.max(np.abs(mps.lam[q + 1] - s[:k] / np.linalg.norm(s[:k]))) <= 1e-12
+    assert abs(mps.stats.discarded_weight - (1 - np.sum(s[:k] ** 2) / np.sum(s ** 2))) <= 1e-12
+
+
 # -- planted mistakes: each must be caught by the pins above ------------------
 
 def _bad_apply_2q_scaled_c(mps, q, u4, chi_max, eps_rel=0.0, svd=None):
