@@ -123,7 +123,7 @@ typedef enum {
   MPS_K_ENV_CHILD = 6, /* child environment */
   MPS_K_ENV_LEAF = 7,  /* leaf expectation values */
   MPS_K_ENV_TRACE = 8, /* trace expectation values */
-  MPS_K_REDUCE = 9,    /* FP64 energy sum */
+  MPS_K_REDUCE = 9,    /* FP64 energy sum and observable row sums */
   MPS_K_COUNT = 10
 } mps_kernel_kind;
 
