@@ -72,7 +72,7 @@ def commutator_rows(ham, pool: np.ndarray):
 class AdaptResult:
     chosen: list  # pool indices, in circuit order
     theta: np.ndarray
-    energy: float
+    energy: float  # measured energy of the final circuit; None if no string was added
     converged: bool  # largest pool gradient fell below grad_tol
     energies: list = field(default_factory=list)  # energy after each growth step
     max_gradients: list = field(default_factory=list)

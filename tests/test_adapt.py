@@ -154,3 +154,12 @@ def test_adapt_random_molecule_descends_and_is_variational():
     assert res.energies[0] < e_hf - 1e-3
     assert np.all(np.diff(res.energies) <= 1e-10)
     assert res.energy >= sector_ground_energy(ham, n_e) - 1e-10
+
+
+def test_commuting_pool_strings_give_empty_rows_and_adapt_stops():
+    ham = h2_sto3g()
+    pool = np.array([[0, 0, 0, 0], [3, 3, 0, 0], [2, 1, 1, 1]], np.uint8)  # I and ZZ commute with every Z/I term
+    strings, row_ptr, cols, w = commutator_rows(ham, pool)
+    assert row_ptr[1] == row_ptr[0] and row_ptr.size == 4 and row_ptr[-1] == cols.size
+    res = qubit_adapt(pool, 4, lambda t, th: np.zeros(pool.shape[0]), lambda t: None, max_ops=3, grad_tol=1e-6)
+    assert res.converged and res.chosen == [] and res.energy is None and res.max_gradients == [0.0]

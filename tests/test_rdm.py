@@ -114,3 +114,18 @@ def test_rows_on_oracle_string_values_give_the_oracle_rdms(state):
         assert np.max(np.abs(out[k] - ref)) <= 1e-12, k
     if state == "brickwork":
         assert np.max(np.abs(g1.imag)) > 1e-3  # complex RDMs: the imaginary weights matter
+
+
+def test_row_builder_arguments_and_layout():
+    with pytest.raises(ValueError):
+        rdm_rows(5, "1rdm")
+    with pytest.raises(ValueError):
+        rdm_rows(4, "3rdm")
+    strings, row_ptr, cols, w, layout = merged_rows(4, ("1rdm", "D"))
+    assert [(k, off, shape) for k, off, shape in layout] == [("1rdm", 0, (4, 4)), ("D", 16, (2, 2))]
+    assert row_ptr.size == 16 + 4 + 1 and row_ptr[0] == 0 and np.all(np.diff(row_ptr) >= 0)
+    assert cols.min() >= 0 and cols.max() < strings.shape[0] and row_ptr[-1] == cols.size == w.size
+    assert len({s.tobytes() for s in strings}) == strings.shape[0]
+    # vanishing monomials (a+_P a+_P) give empty rows
+    _, rp2, _, _, _ = rdm_rows(4, "2rdm")
+    assert rp2[1] - rp2[0] == 0  # Gamma[0, 0, 0, 0]

@@ -157,3 +157,18 @@ def test_random_molecule_is_variational_and_monotone():
     assert e_exact - 1e-10 <= res.energy < e_hf - 1e-3
     # the measured energy at the returned angles is the reported one
     assert abs(f(res.theta[None])[0] - res.energy) <= 1e-12
+
+
+def test_edge_cases():
+    def const(thetas):
+        return np.full(np.atleast_2d(thetas).shape[0], 2.5)
+
+    res = sequential_minimize(const, np.zeros(0))  # no angles: the start and end-of-sweep energies only
+    assert res.converged and res.energy == 2.5 and res.n_evals == 2 and res.theta.shape == (0,)
+    assert np.array_equal(shift_gradient(const, np.zeros(3)), np.zeros(3))
+    res = bfgs_minimize(const, np.zeros(3))  # flat: zero gradient at once
+    assert res.converged and res.iterations == 1 and res.energy == 2.5
+    with pytest.raises(ValueError):
+        trig_coefficients(np.zeros(4))
+    with pytest.raises(ValueError):
+        sequential_minimize(lambda t: np.zeros(1), np.zeros(2))  # wrong number of energies
