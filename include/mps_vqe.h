@@ -44,7 +44,9 @@ typedef enum {
   MPS_ENOMEM = 2,     /* device allocation failed or the allocation cap was hit */
   MPS_ECUDA = 3,      /* a CUDA runtime call failed */
   MPS_ETIMEOUT = 4,   /* a bounded device-side wait ran out */
-  MPS_ENOTCONV = 5,   /* the Jacobi SVD hit its sweep cap (result still written) */
+  MPS_ENOTCONV = 5,   /* reserved: an SVD that hits its sweep cap does not fail the call; its
+                         result is written as it stands and counted in
+                         mps_report.svd_not_converged */
   MPS_EBUSY = 6,      /* serving queue full */
   MPS_ESTATE = 7      /* state left inconsistent by an earlier failure: reset it */
 } mps_status;
