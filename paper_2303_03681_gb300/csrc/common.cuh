@@ -156,8 +156,9 @@ __device__ __forceinline__ bool jacobi_rotation(S alpha, S beta, S gr, S gi, S t
 // an SM with two FP64 FMA units, so the angle is found in FP32 on Gram
 // entries scaled by a power of two near |g|, and (c, s e^{i phi}) is then
 // brought to unit norm in FP64 by c^2 + |s|^2 = 1 + d -> scale by
-// 1 - d/2 + 3 d^2 / 8 (|d| ~ 1e-7, so the rotation is unitary to FP64
-// rounding).  The angle itself is only FP32-accurate, which costs at most
+// 1 - d/2 + 3 d^2 / 8, the first terms of the binomial series of
+// (1 + d)^(-1/2) (|d| ~ 1e-7, so the dropped O(d^3) term leaves the
+// rotation unitary to FP64 rounding).  The angle itself is only FP32-accurate, which costs at most
 // an extra sweep: a pair left with |g| ~ 1e-7 |g| is rotated again.
 template <>
 __device__ __forceinline__ bool jacobi_rotation<double>(double alpha, double beta, double gr, double gi, double tol,
