@@ -170,6 +170,26 @@ def _symplectic_to_ops(rows, n):
     return ops
 
 
+def ops_to_symplectic(ops: np.ndarray):
+    """I/X/Y/Z strings (T, n) uint8 -> packed (x, z) bit words, each (T, W)
+    uint64 with site j at bit j % 64 of word j // 64 (X: x, Y: x and z, Z: z)."""
+    ops = np.asarray(ops, dtype=np.uint8)
+    T, n = ops.shape
+    w = _n_words(n)
+    out = []
+    for bits in ((ops == OP_X) | (ops == OP_Y), (ops == OP_Y) | (ops == OP_Z)):
+        pad = np.zeros((T, 64 * w), dtype=bool)
+        pad[:, :n] = bits
+        packed = np.packbits(pad, axis=1, bitorder="little")  # (T, 8 w) bytes, bit j of byte j // 8
+        out.append(np.ascontiguousarray(packed).view("<u8").astype(np.uint64).reshape(T, w))
+    return out[0], out[1]
+
+
+def symplectic_to_ops(x: np.ndarray, z: np.ndarray, n: int) -> np.ndarray:
+    """Inverse of ``ops_to_symplectic``."""
+    return _symplectic_to_ops(np.concatenate([x, z], axis=1), n)
+
+
 def fermion_terms_to_paulis(n_so, terms, tol=1e-12):
     """JW-map a list of fermionic monomials to an exact complex Pauli sum.
 

@@ -163,3 +163,42 @@ def test_commuting_pool_strings_give_empty_rows_and_adapt_stops():
     assert row_ptr[1] == row_ptr[0] and row_ptr.size == 4 and row_ptr[-1] == cols.size
     res = qubit_adapt(pool, 4, lambda t, th: np.zeros(pool.shape[0]), lambda t: None, max_ops=3, grad_tol=1e-6)
     assert res.converged and res.chosen == [] and res.energy is None and res.max_gradients == [0.0]
+
+
+def test_symplectic_products_on_several_words():
+    """Packed-word phases and products against a per-site table on 70- and
+    130-qubit strings (two and three 64-bit words)."""
+    from paper_2303_03681_gb300.adapt import _pauli_product_phase
+    from paper_2303_03681_gb300.inputs.hamiltonian import ops_to_symplectic, symplectic_to_ops
+
+    # sigma_a sigma_b = i^E[a, b] sigma_{a xor b} for I, X, Y, Z = 0, 1, 2, 3
+    E = np.array([[0, 0, 0, 0], [0, 0, 1, 3], [0, 3, 0, 1], [0, 1, 3, 0]])
+    rng = make_rng(MASTER_SEED + 104)
+    for n in (70, 130):
+        A = rng.integers(0, 4, (300, n)).astype(np.uint8)
+        B = rng.integers(0, 4, n).astype(np.uint8)
+        ax, az = ops_to_symplectic(A)
+        bx, bz = ops_to_symplectic(B[None])
+        assert np.array_equal(symplectic_to_ops(ax, az, n), A)
+        e = _pauli_product_phase(ax, az, bx[0], bz[0])
+        assert np.array_equal(e, E[A, B[None, :]].sum(axis=1) % 4)
+        assert np.array_equal(symplectic_to_ops(ax ^ bx[0], az ^ bz[0], n), A ^ B[None, :])
+
+
+def test_pool_chunks_cover_the_pool_within_the_cap():
+    from paper_2303_03681_gb300.adapt import pool_chunks
+
+    h, g = random_integrals(4, make_rng(MASTER_SEED + 105))
+    ham = jw_molecular_hamiltonian(h, g)
+    pool = windowed_gsd_pool(4)
+    _, row_ptr, _, _ = commutator_rows(ham, pool)
+    sizes = np.diff(row_ptr)
+    cap = int(sizes.max() * 5)
+    chunks = pool_chunks(ham, pool, cap)
+    assert chunks[0][0] == 0 and chunks[-1][1] == pool.shape[0]
+    assert all(a[1] == b[0] for a, b in zip(chunks, chunks[1:]))
+    assert all(sizes[lo:hi].sum() <= cap for lo, hi in chunks) and len(chunks) > 1
+    # per-chunk rows equal the slices of the whole-pool rows
+    for lo, hi in chunks:
+        s2, rp2, c2, w2 = commutator_rows(ham, pool[lo:hi])
+        assert np.array_equal(np.diff(rp2), sizes[lo:hi])
