@@ -413,6 +413,13 @@ def run_gpu(args):
         "hbm_bytes_allocated": hbm_bytes,
         "wall_s_timed_region": wall,
     }
+    if not args.no_oracle_check:
+        try:
+            chk = oracle_check(mps, states[0], C, H, w, w["trunc"])
+        except Exception as exc:  # an auxiliary field never costs the bench line
+            chk = {"error": f"{type(exc).__name__}: {exc}"}
+        if chk is not None:
+            line["oracle_check"] = chk
     if args.serve_requests > 0:
         line["serving"] = serve_phase(mps, local, C, H, w, args, rate=0.9 * value / world)
     if world == 1 and not args.no_cpu_baseline:
@@ -454,6 +461,29 @@ def serve_phase(mps, device, C, H, w, args, rate):
             "hbm_peak_bytes": st["peak_bytes"]}
 
 
+def oracle_check(mps, state, C, H, w, trunc_rel):
+    """|E_gpu - E_oracle| for this workload at the reference angles of a
+    stored oracle energy (tests/golden/*_oracle.json, written by a committed
+    script that runs only the oracle), or None when no record matches."""
+    import glob
+
+    for path in sorted(glob.glob(os.path.join(ROOT, "tests", "golden", "*_oracle.json"))):
+        rec = json.load(open(path))
+        if rec.get("workload") != w["desc"]["workload"] or rec.get("trunc_rel") != trunc_rel:
+            continue
+        lo, hi = rec["theta_range"]
+        theta = make_rng(rec["theta_seed"]).uniform(lo, hi, w["tmpl"].n_params)
+        e, status = mps.vqe_eval_batch([(state, C, H, theta, w["bits"])])
+        if status[0] != 0:
+            return {"error": f"status {int(status[0])}"}
+        return {"reference": os.path.relpath(path, ROOT), "theta_seed": rec["theta_seed"],
+                "energy_gpu": float(e[0]), "energy_oracle": rec["oracle_energy"],
+                "abs_error_ha": abs(float(e[0]) - rec["oracle_energy"]),
+                "discarded_weight_gpu": state.report()["discarded_weight"],
+                "discarded_weight_oracle": rec["oracle_discarded_weight"]}
+    return None
+
+
 def merge_profiles(profs):
     out = {}
     for p in profs:
@@ -477,6 +507,8 @@ def main():
                     help="Jacobi SVD: fp64 = FP64-accurate (complex64 states: FP32 sweeps, then FP64 ones), "
                          "fp64-all = every sweep in FP64, fp32 = FP32 sweeps only")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-oracle-check", action="store_true",
+                    help="skip the extra evaluation at the stored oracle energy's reference angles")
     ap.add_argument("--batch", type=int, default=8, help="concurrent evaluations per step")
     ap.add_argument("--tensor-cores", type=int, choices=[0, 1], default=1,
                     help="complex64 environment contractions on tcgen05 (1) or CUDA cores (0)")
