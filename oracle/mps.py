@@ -29,6 +29,9 @@ Readings where the paper is silent (stated once, used throughout):
 from dataclasses import dataclass, field
 
 import numpy as np
+import scipy.linalg
+
+from . import svd_jacobi
 
 PAULI = {
     0: np.eye(2, dtype=complex),
@@ -91,10 +94,30 @@ def truncation_rank(s: np.ndarray, chi_max: int, eps_rel: float) -> int:
     return max(1, min(k, int(chi_max)))
 
 
+def svd_robust(A: np.ndarray):
+    """SVD of Eq. svdtildeC, A = U diag(s) Vh with s descending.
+
+    LAPACK's divide-and-conquer driver (zgesdd) is tried first.  It can stop
+    with "SVD did not converge" on some inputs (seen on an aarch64 OpenBLAS
+    build), so the QR-iteration driver (zgesvd) is tried next, and the
+    one-sided Jacobi SVD of Algorithm 1 (``svd_jacobi``) last.  All three
+    compute the same decomposition; only the rounding differs."""
+    try:
+        return np.linalg.svd(A, full_matrices=False)
+    except np.linalg.LinAlgError:
+        pass
+    try:
+        return scipy.linalg.svd(A, full_matrices=False, lapack_driver="gesvd")
+    except (np.linalg.LinAlgError, ValueError):
+        pass
+    return svd_jacobi.one_sided_jacobi_svd(A)
+
+
 def apply_2q(mps: MPS, q: int, u4: np.ndarray, chi_max: int, eps_rel: float = 0.0,
              svd=None) -> None:
     """Two-qubit gate on sites (q, q+1) with the Hastings update (Methods,
-    Eqs. tildeC, svdtildeC and Bl).  ``svd`` defaults to LAPACK (zgesdd)."""
+    Eqs. tildeC, svdtildeC and Bl).  ``svd`` defaults to ``svd_robust``
+    (LAPACK zgesdd, with zgesvd and Algorithm 1 as fallbacks)."""
     Bl, Br = mps.B[q], mps.B[q + 1]
     chi_l, chi_r = Bl.shape[0], Br.shape[2]
     theta = np.einsum("aim,mjb->aijb", Bl, Br)
@@ -104,7 +127,7 @@ def apply_2q(mps: MPS, q: int, u4: np.ndarray, chi_max: int, eps_rel: float = 0.
     Ct = mps.lam[q][:, None] * C.reshape(chi_l, 4 * chi_r)
     Ct = Ct.reshape(2 * chi_l, 2 * chi_r)
     if svd is None:
-        _, s, Vh = np.linalg.svd(Ct, full_matrices=False)
+        _, s, Vh = svd_robust(Ct)
     else:
         _, s, Vh = svd(Ct)
     k = truncation_rank(s, chi_max, eps_rel)

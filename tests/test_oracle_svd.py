@@ -58,3 +58,27 @@ def test_mps_with_jacobi_svd_matches_lapack_route():
     for la, lb in zip(a.lam, b.lam):
         assert np.allclose(la, lb, rtol=1e-11, atol=1e-13)
     assert om.fidelity(a, b) >= 1 - 1e-12
+
+
+def _raise_linalg(*args, **kwargs):
+    raise np.linalg.LinAlgError("SVD did not converge")
+
+
+@pytest.mark.parametrize("fail", ["gesdd", "gesdd+gesvd"])
+def test_oracle_svd_fallback_matches_lapack_route(monkeypatch, fail):
+    """When LAPACK's zgesdd stops with 'SVD did not converge' (it did on an
+    aarch64 host), the oracle's gate update falls back to zgesvd and then to
+    the Jacobi SVD of Algorithm 1; the truncated MPS is the same."""
+    circ = brickwork_circuit(10, 8, make_rng(41))
+    ref = om.run_circuit(10, None, circ, chi_max=12, eps_rel=1e-10)
+    monkeypatch.setattr(om.np.linalg, "svd", _raise_linalg)
+    if fail == "gesdd+gesvd":
+        monkeypatch.setattr(om.scipy.linalg, "svd", _raise_linalg)
+    got = om.run_circuit(10, None, circ, chi_max=12, eps_rel=1e-10)
+    monkeypatch.undo()
+    assert ref.bond_dims() == got.bond_dims()
+    for la, lb in zip(ref.lam, got.lam):
+        assert np.allclose(la, lb, rtol=1e-10, atol=1e-13)
+    assert abs(ref.stats.discarded_weight - got.stats.discarded_weight) <= 1e-12
+    assert om.fidelity(ref, got) >= 1 - 1e-12
+    assert abs(om.canonical_residual(got) - om.canonical_residual(ref)) <= 1e-10
