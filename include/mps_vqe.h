@@ -44,9 +44,12 @@ typedef enum {
   MPS_ENOMEM = 2,     /* device allocation failed or the allocation cap was hit */
   MPS_ECUDA = 3,      /* a CUDA runtime call failed */
   MPS_ETIMEOUT = 4,   /* a bounded device-side wait ran out */
-  MPS_ENOTCONV = 5,   /* reserved: an SVD that hits its sweep cap does not fail the call; its
-                         result is written as it stands and counted in
-                         mps_report.svd_not_converged */
+  MPS_ENOTCONV = 5,   /* a truncation SVD reached its Jacobi sweep cap (Algorithm 1's
+                         stopping test was not met).  The result is still delivered: the
+                         state is updated and the energy written with that SVD as it stood,
+                         and the state stays usable.  Counted in
+                         mps_report.svd_not_converged.  Returned by mps_apply_gates,
+                         vqe_eval, vqe_eval_batch (per request) and vqe_poll. */
   MPS_EBUSY = 6,      /* serving queue full */
   MPS_ESTATE = 7      /* state left inconsistent by an earlier failure: reset it */
 } mps_status;
@@ -63,10 +66,11 @@ typedef struct {
   int32_t precision;      /* mps_precision */
   double trunc_rel;       /* keep s_i > trunc_rel * s_1 (0: keep all nonzero) */
   int32_t svd_fp64;       /* 0: Jacobi SVD in the storage precision;
-                             1: FP64-accurate Jacobi SVD (for complex64 states with 96 or more
-                                theta columns: FP32 sweeps to FP32 convergence, one FP64
-                                re-orthonormalisation of V, A = C~ V rebuilt in FP64, FP64 sweeps
-                                to the FP64 stopping rule);
+                             1: FP64-accurate Jacobi SVD (thetas whose column capacity is 32 or
+                                more: FP32 sweeps to FP32 convergence, two FP64
+                                re-orthonormalisation passes of V, A = C~ V rebuilt in FP64, FP64
+                                sweeps to the FP64 stopping rule; smaller thetas: every sweep in
+                                FP64);
                              2: every Jacobi sweep in FP64 */
   int32_t svd_max_sweeps; /* Jacobi sweep cap; 0 selects 60 */
   double svd_tol;         /* rotate a pair while |b_ij| > tol sqrt(b_ii b_jj); 0: default */
@@ -184,7 +188,10 @@ void mps_destroy(mps_state* st);
  * two-qubit: Hastings update of Eqs. tildeC, svdtildeC, Bl with truncation
  * to min(chi_max, #{s_i > trunc_rel s_1}) and renormalisation of the kept
  * singular values).  `report` (nullable) receives the accumulated
- * statistics; this call synchronises the stream. */
+ * statistics; this call synchronises the stream.  MPS_ENOTCONV when an SVD
+ * issued since the host last read the state's report (this call, or
+ * asynchronous circuits before it; mps_reset clears the count) reached its
+ * sweep cap: the gates are applied and the report is filled all the same. */
 mps_status mps_apply_gates(mps_state* st, const mps_gate* gates, size_t n, mps_report* report);
 
 /* Upload a circuit template (see mps_template_gate) with n_params angles. */
@@ -255,7 +262,10 @@ mps_status mps_get_report(mps_state* st, mps_report* out);
 /* One VQE energy evaluation per request: reset to init_bits, apply the
  * template bound to theta, evaluate the Hamiltonian.  Requests run in order
  * on the context stream; energies_out[i] (host) and status_out[i]
- * (nullable) receive the results.  theta and init_bits are host arrays. */
+ * (nullable) receive the results.  theta and init_bits are host arrays.
+ * A request whose circuit had an SVD reach its sweep cap gets MPS_ENOTCONV
+ * with its energy written; other failures write 0.  The return value is the
+ * first status that is not MPS_OK. */
 typedef struct {
   mps_state* state;
   const mps_circuit* circuit;
@@ -276,13 +286,16 @@ mps_status vqe_eval(mps_ctx* ctx, const vqe_request* reqs, size_t n, double* ene
  * Streams beyond the device's hardware work queues are serialised by the
  * driver: set CUDA_DEVICE_MAX_CONNECTIONS (up to 32) to at least the number
  * of contexts before the process creates its CUDA context.
- * energies_out[i] / status_out[i] (host, status nullable) as in vqe_eval;
- * the return value is the first failing status, or MPS_OK. */
+ * energies_out[i] / status_out[i] (host, status nullable) as in vqe_eval
+ * (MPS_ENOTCONV included); the return value is the first status that is not
+ * MPS_OK. */
 mps_status vqe_eval_batch(const vqe_request* reqs, size_t n, double* energies_out, mps_status* status_out);
 /* Same with device-resident data: every request's theta is a device pointer
  * and d_energies_out is a device array of n doubles.  The call returns once
  * all work is issued (each energy reads its state's bond dimensions, which
- * waits for that state's circuit); synchronise the streams before reading. */
+ * waits for that state's circuit); synchronise the streams before reading.
+ * Sweep-cap hits are not reported here (the call returns before the SVDs
+ * run): read mps_report.svd_not_converged of each state afterwards. */
 mps_status vqe_eval_batch_async(const vqe_request* reqs, size_t n, double* d_energies_out, mps_status* status_out);
 
 /* ---- serving: continuous batching of energy evaluations -----------------
@@ -312,8 +325,9 @@ mps_status mps_server_add_fragment(mps_server* srv, const mps_circuit* circuit, 
 mps_status vqe_submit(mps_server* srv, int32_t fragment, const double* theta, uint64_t* ticket_out);
 /* Wait up to timeout_ms (0 = do not wait, < 0 = forever) for a request.
  * Returns MPS_OK with the energy and the submit-to-completion latency in
- * milliseconds, MPS_ETIMEOUT if it is not done yet, MPS_EINVAL for an unknown
- * ticket, or the request's own failure status.  A completed ticket is
+ * milliseconds (MPS_ENOTCONV with both when an SVD of the evaluation reached
+ * its sweep cap), MPS_ETIMEOUT if it is not done yet, MPS_EINVAL for an
+ * unknown ticket, or the request's own failure status.  A completed ticket is
  * released by the poll that returns it. */
 mps_status vqe_poll(mps_server* srv, uint64_t ticket, int32_t timeout_ms, double* energy_out, double* latency_ms_out);
 /* Counters: requests completed, currently admitted, queued; device bytes the
@@ -351,9 +365,12 @@ void mps_server_destroy(mps_server* srv);
  *   gate     host array, 4x4 row-major complex (32 doubles), index 2 i_q + i_{q+1};
  *   chi_max, trunc_rel  truncation as in mps_config;
  *   chi_out  receives k (one int32).
- * The update is the one mps_apply_gates makes for a complex128 state.  The
- * call returns after issuing the work; synchronise the stream before reading
- * the outputs.  The first call on each device sets the library up for that
+ * The update is the one mps_apply_gates makes for a complex128 state, except
+ * that SVD convergence is not reported: the call returns before the work
+ * runs, and an SVD that reaches the sweep cap (60 sweeps) is written as it
+ * stands.  The call returns after issuing the work; synchronise the stream
+ * before reading the outputs.  MPS_EINVAL for a device that does not exist
+ * (checked before anything is issued or cached).  The first call on each device sets the library up for that
  * device (it looks up the scratch array's device address); make it before
  * any stream capture.  All calls share the scratch array and it keeps the
  * last call's contents (the kernels overwrite what they read): calls whose

@@ -107,12 +107,12 @@ struct DevReport {
   double inv_norm;  // 1 / ||kept s|| of the last two-qubit gate (read by the G3 kernel)
   int max_chi;
   int degenerate_cuts;
-  int not_converged;
+  int not_converged;  // SVDs that reached the sweep cap
+  int tc_error;       // a tensor-core kernel ran out of its bounded wait (read with not_converged in one copy)
   int max_sweeps;
+  int pad;
   long long two_qubit_gates;
   double svd_flops;
-  int tc_error;  // a tensor-core kernel ran out of its bounded wait
-  int pad;
   long long sweeps_fp32, sweeps_fp64;  // Jacobi sweeps run, summed over SVDs
   double phase_cycles[4];              // cluster SVD phases (CTA 0 clock): load, FP32 sweeps, V / A rebuild, FP64 sweeps + output
 };
@@ -131,17 +131,11 @@ struct SvdParams {
 // alpha = a_i^H a_i, beta = a_j^H a_j, g = gr + i gi = a_i^H a_j (Algorithm 1
 // of the paper, with the phase of g moved onto column j): the new columns are
 // a_i' = c a_i - conj(s e^{i phi}) a_j and a_j' = c a_j + s e^{i phi} a_i.
-// Returns false when the pair is left alone: already orthogonal to tol, a
-// column at the rounding floor, or both columns with squared norm <= tau2.
-// With tau2 = eps_rel^2 ||A||_F^2 / n^2 (n columns) the columns below it
-// hold at most eps_rel^2 ||A||_F^2 / n <= (eps_rel s_1)^2 together, so
-// whatever their mutual angles, their singular values fall below the
-// truncation threshold eps_rel s_1; they only have to be orthogonalised
-// against the larger columns, which stay exact.
+// Returns false when the pair is left alone: already orthogonal to tol, or a
+// column at the rounding floor.
 template <typename S>
-__device__ __forceinline__ bool jacobi_rotation(S alpha, S beta, S gr, S gi, S tol, S floor, S tiny, S tau2, S& c,
+__device__ __forceinline__ bool jacobi_rotation(S alpha, S beta, S gr, S gi, S tol, S floor, S tiny, S& c,
                                                 cplx<S>& sph) {
-  if (!(max(alpha, beta) > tau2)) return false;
   const S mag = sqrt(gr * gr + gi * gi);
   if (!(mag > tiny) || !(mag > tol * sqrt(alpha * beta)) || !(min(alpha, beta) > floor)) return false;
   const S zeta = (beta - alpha) / (S(2) * mag);
@@ -162,9 +156,7 @@ __device__ __forceinline__ bool jacobi_rotation(S alpha, S beta, S gr, S gi, S t
 // an extra sweep: a pair left with |g| ~ 1e-7 |g| is rotated again.
 template <>
 __device__ __forceinline__ bool jacobi_rotation<double>(double alpha, double beta, double gr, double gi, double tol,
-                                                        double floor, double tiny, double tau2, double& c,
-                                                        cplx<double>& sph) {
-  if (!(max(alpha, beta) > tau2)) return false;
+                                                        double floor, double tiny, double& c, cplx<double>& sph) {
   const double mag2 = gr * gr + gi * gi;
   if (!(mag2 > tiny) || !(mag2 > tol * tol * alpha * beta) || !(min(alpha, beta) > floor)) return false;
   // 2^-h with 2^(2h) ~ mag2 (mag2 is a normal double here)
@@ -185,6 +177,104 @@ __device__ __forceinline__ bool jacobi_rotation<double>(double alpha, double bet
   c = cd * f;
   sph = cmk<double>(sr * f, si * f);
   return true;
+}
+
+// The pair rules of the truncation SVD (tail columns).  Jacobi only has to
+// make the columns that the truncation keeps orthogonal to each other and to
+// all others; the columns it discards may stay mixed among themselves as long
+// as none of their singular values could reach the cut.  At the start of a
+// sweep, from the squared column norms nrm2[0..n): the kept set K is what the
+// truncation would keep now (nrm2 > trunc_rel^2 max nrm2, the chi_max largest
+// by rank when more pass), D the rest, and the cut is trunc_rel^2 max nrm2 (or
+// the smallest kept nrm2 under a chi_max cut).  The class of column c goes to
+// cls[c]:
+//  * kTailSkip when sum_D nrm2 <= cut / 4: every singular value of the D
+//    block is then at most half of every kept column's norm, so once K is
+//    orthogonal to itself and to D, K holds the leading singular vectors
+//    whatever D looks like (and the discarded weight is sum_D nrm2); pairs of
+//    two such columns are not rotated.  The factor 1/4 also bounds how much
+//    rotating a kept column against one D column disturbs its orthogonality
+//    to the others, so the kept columns converge quickly (a bare per-column
+//    threshold did not: a column just above it never converged against mixed
+//    columns just below it).
+//  * kTailLoose otherwise, for D columns with nrm2 <= cut / 4: pairs of two
+//    of them are rotated only while |g| > loose_tol sqrt(b_ii b_jj) with
+//    loose_tol = 2 / n.  By Gershgorin on their Gram matrix the singular
+//    values of that block then stay below (cut / 4)(1 + n loose_tol) < cut.
+//  * 0 for every other column (the normal stopping rule).
+// Every thread of the block calls it; blocks with the same nrm2 and size
+// compute the same classes.
+constexpr int kTailLoose = 1, kTailSkip = 2;
+
+__device__ __forceinline__ void truncation_tail(const double* nrm2, int n, double trunc_rel, int chi_max, int* cls) {
+  __shared__ double s_red[33];
+  __shared__ int s_cnt;
+  __shared__ double s_cut;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  // largest squared norm
+  double mx = 0.0;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) mx = fmax(mx, nrm2[c]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) s_red[warp] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < nw; ++w) v = fmax(v, s_red[w]);
+    s_red[32] = v;
+    s_cnt = 0;
+  }
+  __syncthreads();
+  const double thr = trunc_rel * trunc_rel * s_red[32];
+  int cnt = 0;
+  for (int c = threadIdx.x; c < n; c += blockDim.x) cnt += nrm2[c] > thr;
+  cnt = __reduce_add_sync(0xffffffffu, cnt);
+  if (lane == 0) atomicAdd(&s_cnt, cnt);
+  __syncthreads();
+  const bool by_rank = s_cnt > chi_max;
+  if (threadIdx.x == 0) s_cut = thr;
+  __syncthreads();
+  // kept flags (1 = kept) into cls[] first
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    if (by_rank) {
+      const double v = nrm2[c];
+      int rk = 0;
+      for (int h = 0; h < n; ++h) rk += (nrm2[h] > v) || (nrm2[h] == v && h < c);
+      cls[c] = rk < chi_max;
+      if (rk == chi_max - 1) s_cut = v;
+    } else {
+      cls[c] = nrm2[c] > thr;
+    }
+  }
+  __syncthreads();
+  // weight of D, summed in a fixed order
+  double part = 0.0;
+  for (int c = threadIdx.x; c < n; c += blockDim.x)
+    if (!cls[c]) part += nrm2[c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  __syncthreads();
+  if (lane == 0) s_red[warp] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < nw; ++w) v += s_red[w];
+    s_red[32] = v;
+  }
+  __syncthreads();
+  const double cut = s_cut;
+  const bool skip = s_red[32] <= 0.25 * cut;
+  for (int c = threadIdx.x; c < n; c += blockDim.x)
+    cls[c] = cls[c] ? 0 : (skip ? kTailSkip : (nrm2[c] <= 0.25 * cut ? kTailLoose : 0));
+  __syncthreads();
+}
+
+// The stopping tolerance of a pair from the classes of its columns (see
+// truncation_tail): a negative value means the pair is not rotated.
+template <typename S>
+__device__ __forceinline__ S pair_tol(int ci, int cj, S tol, S loose) {
+  const int c = min(ci, cj);
+  return c == kTailSkip ? S(-1) : (c == kTailLoose ? max(tol, loose) : tol);
 }
 
 }  // namespace mpsv

@@ -353,19 +353,28 @@ static void destroy_ham(mps_ham* h) {
 
 using namespace mpsv;
 
-// Queues a read of the tensor-core timeout flag; *flag is valid after the
-// stream synchronises.
-static cudaError_t queue_tc_flag(mps_state* st, int* flag) {
-  *flag = 0;
-  if (!st->tc) return cudaSuccess;
-  return cudaMemcpyAsync(flag, &st->d_rep->tc_error, sizeof(int), cudaMemcpyDeviceToHost, st->ctx->stream);
+namespace mpsv {
+
+cudaError_t queue_flags(mps_state* st, StateFlags* f) {
+  f->not_converged = 0;
+  f->tc_error = 0;
+  return cudaMemcpyAsync(f, &st->d_rep->not_converged, sizeof(StateFlags), cudaMemcpyDeviceToHost, st->ctx->stream);
 }
 
-static mps_status tc_flag_status(int flag) {
-  if (!flag) return MPS_OK;
-  set_error("energy: a tensor-core contraction ran out of its bounded wait");
-  return MPS_ETIMEOUT;
+mps_status flags_status(const StateFlags& f, bool gates) {
+  if (f.tc_error) {
+    set_error("energy: a tensor-core contraction ran out of its bounded wait");
+    return MPS_ETIMEOUT;
+  }
+  if (gates && f.not_converged) {
+    set_error("%d truncation SVDs reached the Jacobi sweep cap; their results were used as they stand",
+              f.not_converged);
+    return MPS_ENOTCONV;
+  }
+  return MPS_OK;
 }
+
+}  // namespace mpsv
 
 extern "C" {
 
@@ -455,8 +464,8 @@ mps_status mps_energy(mps_state* st, const mps_ham* h, double* energy_out, doubl
   mps_status rc = ham_energy_async(st, hh, nullptr);
   if (rc != MPS_OK) return rc;
   MPSV_CUDA(cudaMemcpyAsync(energy_out, st->d_energy, sizeof(double), cudaMemcpyDeviceToHost, st->ctx->stream));
-  int tc_flag = 0;
-  MPSV_CUDA(queue_tc_flag(st, &tc_flag));
+  StateFlags flags;
+  MPSV_CUDA(queue_flags(st, &flags));
   if (norm_out) {
     // sum of lam^2 on bond 1 (the first inner bond; bond 0 is the trivial edge)
     const int b = st->n > 1 ? 1 : 0;
@@ -473,7 +482,7 @@ mps_status mps_energy(mps_state* st, const mps_ham* h, double* energy_out, doubl
     *norm_out = s;
   }
   MPSV_CUDA(cudaStreamSynchronize(st->ctx->stream));
-  return tc_flag_status(tc_flag);
+  return flags_status(flags, false);
 }
 
 mps_status mps_expectations(mps_state* st, const mps_ham* h, double* values_out) {
@@ -488,10 +497,10 @@ mps_status mps_expectations(mps_state* st, const mps_ham* h, double* values_out)
   if (h->n_terms)
     MPSV_CUDA(cudaMemcpyAsync(values_out, st->d_vals, h->n_terms * sizeof(double), cudaMemcpyDeviceToHost,
                               st->ctx->stream));
-  int tc_flag = 0;
-  MPSV_CUDA(queue_tc_flag(st, &tc_flag));
+  StateFlags flags;
+  MPSV_CUDA(queue_flags(st, &flags));
   MPSV_CUDA(cudaStreamSynchronize(st->ctx->stream));
-  return tc_flag_status(tc_flag);
+  return flags_status(flags, false);
 }
 
 mps_status vqe_eval(mps_ctx* ctx, const vqe_request* reqs, size_t n, double* energies_out,
@@ -515,13 +524,13 @@ mps_status vqe_eval(mps_ctx* ctx, const vqe_request* reqs, size_t n, double* ene
     if (rc == MPS_OK) {
       cudaError_t e = cudaMemcpyAsync(&energies_out[i], r.state->d_energy, sizeof(double), cudaMemcpyDeviceToHost,
                                       ctx->stream);
-      int tc_flag = 0;
-      if (e == cudaSuccess) e = queue_tc_flag(r.state, &tc_flag);
+      StateFlags flags;
+      if (e == cudaSuccess) e = queue_flags(r.state, &flags);
       if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-      rc = e != cudaSuccess ? cuda_fail(e, "vqe_eval") : tc_flag_status(tc_flag);
+      rc = e != cudaSuccess ? cuda_fail(e, "vqe_eval") : flags_status(flags, true);
     }
     if (rc != MPS_OK) {
-      energies_out[i] = 0.0;
+      if (!status_has_result(rc)) energies_out[i] = 0.0;
       if (first_bad == MPS_OK) first_bad = rc;
     }
     if (status_out) status_out[i] = rc;
@@ -622,7 +631,7 @@ static mps_status run_batch(const vqe_request* reqs, size_t n, double* energies_
       }
   }
   // energies (each reads its bond dimensions once), then the results
-  std::vector<int> tc_flag(n, 0);
+  std::vector<StateFlags> flags(n);
   for (size_t i = 0; i < n; ++i) {
     if (rc[i] != MPS_OK) continue;
     const vqe_request& r = reqs[i];
@@ -631,7 +640,7 @@ static mps_status run_batch(const vqe_request* reqs, size_t n, double* energies_
     if (rc[i] == MPS_OK && !on_device) {
       cudaError_t e = cudaMemcpyAsync(&energies_out[i], r.state->d_energy, sizeof(double), cudaMemcpyDeviceToHost,
                                       r.state->ctx->stream);
-      if (e == cudaSuccess) e = queue_tc_flag(r.state, &tc_flag[i]);
+      if (e == cudaSuccess) e = queue_flags(r.state, &flags[i]);
       if (e != cudaSuccess) rc[i] = cuda_fail(e, "vqe_eval_batch");
     }
   }
@@ -640,10 +649,10 @@ static mps_status run_batch(const vqe_request* reqs, size_t n, double* energies_
     if (rc[i] == MPS_OK && !on_device) {
       DeviceGuard guard(reqs[i].state->ctx->device);
       cudaError_t e = cudaStreamSynchronize(reqs[i].state->ctx->stream);
-      rc[i] = e != cudaSuccess ? cuda_fail(e, "vqe_eval_batch") : tc_flag_status(tc_flag[i]);
+      rc[i] = e != cudaSuccess ? cuda_fail(e, "vqe_eval_batch") : flags_status(flags[i], true);
     }
     if (rc[i] != MPS_OK) {
-      if (!on_device) energies_out[i] = 0.0;
+      if (!on_device && !status_has_result(rc[i])) energies_out[i] = 0.0;
       if (first_bad == MPS_OK) first_bad = rc[i];
     }
     if (status_out) status_out[i] = rc[i];
@@ -785,10 +794,10 @@ mps_status mps_observables_eval(mps_state* st, const mps_obs* o, double* values_
     MPSV_CUDA(cudaMemcpyAsync(values_out, st->d_obs, (size_t)o->n_rows * sizeof(double2), cudaMemcpyDeviceToHost,
                               s));
   }
-  int tc_flag = 0;
-  MPSV_CUDA(queue_tc_flag(st, &tc_flag));
+  StateFlags flags;
+  MPSV_CUDA(queue_flags(st, &flags));
   MPSV_CUDA(cudaStreamSynchronize(s));
-  return tc_flag_status(tc_flag);
+  return flags_status(flags, false);
 }
 
 void mps_observables_destroy(mps_obs* o) { destroy_obs(o); }

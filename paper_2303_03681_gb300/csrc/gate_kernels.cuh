@@ -158,9 +158,11 @@ template <> struct SvdEps<float> {
 // Columns whose squared norm is at most `floor` (the rounding level of A)
 // are left alone: rotating two of them only reshuffles rounding noise, and a
 // rotation against a larger column would move it by less than that noise.
+// Pairs of two columns the truncation discards follow the tail rules
+// (truncation_tail, pair_tol); nrm2 and tail are n-entry shared-memory scratch.
 template <typename S>
-__device__ int jacobi_sweeps(cplx<S>* A, cplx<S>* V, int m, int n, int max_sweeps, S tol, S floor, S tau2,
-                             int* s_flag) {
+__device__ int jacobi_sweeps(cplx<S>* A, cplx<S>* V, int m, int n, int max_sweeps, S tol, S floor, double trunc_rel,
+                             int chi_max, double* nrm2, int* tail, int* s_flag) {
   using C = cplx<S>;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const int nn = n + (n & 1);
@@ -168,6 +170,17 @@ __device__ int jacobi_sweeps(cplx<S>* A, cplx<S>* V, int m, int n, int max_sweep
   const S tiny = SvdEps<S>::tiny();
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
+    for (int j = warp; j < n; j += nwarps) {
+      double acc = 0.0;
+      for (int row = lane; row < m; row += 32) {
+        const C x = A[(size_t)j * m + row];
+        acc += double(x.x) * x.x + double(x.y) * x.y;
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) nrm2[j] = acc;
+    }
+    __syncthreads();
+    truncation_tail(nrm2, n, trunc_rel, chi_max, tail);
     if (threadIdx.x == 0) *s_flag = 0;
     __syncthreads();
     bool rotated = false;
@@ -176,6 +189,8 @@ __device__ int jacobi_sweeps(cplx<S>* A, cplx<S>* V, int m, int n, int max_sweep
         int i, j;
         rr_pair(r, k, nn, i, j);
         if (j >= n) continue;
+        const S tl = pair_tol(tail[i], tail[j], tol, S(2.0 / n));
+        if (tl < S(0)) continue;
         C* ai = A + (size_t)i * m;
         C* aj = A + (size_t)j * m;
         S alpha = 0, beta = 0;
@@ -192,7 +207,7 @@ __device__ int jacobi_sweeps(cplx<S>* A, cplx<S>* V, int m, int n, int max_sweep
         gam.y = warp_sum(gam.y);
         S c;
         C sph;  // s e^{i phi}
-        if (!jacobi_rotation<S>(alpha, beta, gam.x, gam.y, tol, floor, tiny, tau2, c, sph)) continue;
+        if (!jacobi_rotation<S>(alpha, beta, gam.x, gam.y, tl, floor, tiny, c, sph)) continue;
         rotated = true;
         for (int row = lane; row < m; row += 32) {
           const C x = ai[row], y = aj[row];
@@ -274,8 +289,7 @@ __global__ void __launch_bounds__(1024, 1)
   const double fro2 = s_nrm;
   const S floor = S(16.0 * double(SvdEps<S>::unit()) * double(SvdEps<S>::unit()) * fro2);
   __syncthreads();
-  const S tau2 = S(p.trunc_rel * p.trunc_rel * fro2 / (double(n) * double(n)));
-  const int sweeps = jacobi_sweeps<S>(A, V, m, n, p.max_sweeps, tol, floor, tau2, &s_flag);
+  const int sweeps = jacobi_sweeps<S>(A, V, m, n, p.max_sweeps, tol, floor, p.trunc_rel, p.chi_max, sig, perm, &s_flag);
 
   // sigma_j = ||A_j|| (Algorithm 1: column norms)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdarg>
+#include <cstddef>
 #include <cstdio>
 #include <map>
 #include <string>
@@ -122,6 +123,7 @@ struct mps_state {
   size_t total_elems = 0;
   std::vector<uint8_t> last_bits;
   bool broken = false;
+  int nc_seen = 0;  // svd_not_converged as last read by the host (mps_apply_gates)
   // circuit binding workspace (per state, so states sharing a circuit can run concurrently)
   mpsv::DevGate* d_bound = nullptr;
   size_t bound_cap = 0;
@@ -176,6 +178,23 @@ struct mps_ham {
 };
 
 namespace mpsv {
+// The two status flags of a state, read back with one 8-byte copy from
+// &DevReport::not_converged.
+struct StateFlags {
+  int not_converged;  // SVDs that reached the sweep cap since the last reset
+  int tc_error;       // a tensor-core kernel ran out of its bounded wait
+};
+static_assert(offsetof(DevReport, tc_error) == offsetof(DevReport, not_converged) + sizeof(int),
+              "StateFlags mirrors two adjacent DevReport fields");
+// Queues the read of a state's flags into *f (valid once the stream has synchronised).
+cudaError_t queue_flags(mps_state* st, StateFlags* f);
+// The status an evaluation reports for its flags: MPS_ETIMEOUT for a
+// tensor-core timeout, else MPS_ENOTCONV when gates count and an SVD reached
+// its sweep cap (the results are written as they stand), else MPS_OK.
+mps_status flags_status(const StateFlags& f, bool gates);
+// A status that still delivers its result (the energy, the updated state).
+inline bool status_has_result(mps_status s) { return s == MPS_OK || s == MPS_ENOTCONV; }
+
 // state.cu
 mps_status state_apply_device_gates(mps_state* st, const DevGate* d_gates, const int* q, const int* arity, size_t n);
 mps_status state_reset(mps_state* st, const uint8_t* bits);

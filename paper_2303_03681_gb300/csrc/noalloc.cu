@@ -123,7 +123,23 @@ extern "C" mps_status mps_gate2_noalloc(int device, void* cuda_stream, int32_t c
     set_error("mps_gate2_noalloc: chi_max = %d, trunc_rel = %g", chi_max, trunc_rel);
     return MPS_EINVAL;
   }
-  DeviceGuard guard(device);
+  int count = 0;
+  cudaError_t ce = cudaGetDeviceCount(&count);
+  if (ce != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    set_error("mps_gate2_noalloc: no CUDA device %d (%d visible)", device, ce == cudaSuccess ? count : 0);
+    return ce != cudaSuccess ? MPS_ECUDA : MPS_EINVAL;
+  }
+  int prev = -1;
+  ce = cudaGetDevice(&prev);
+  if (ce == cudaSuccess && prev != device) ce = cudaSetDevice(device);
+  if (ce != cudaSuccess) return cuda_fail(ce, "mps_gate2_noalloc: cudaSetDevice");
+  struct Restore {
+    int prev, dev;
+    ~Restore() {
+      if (prev >= 0 && prev != dev) cudaSetDevice(prev);
+    }
+  } restore{prev, device};
   unsigned char* scratch = nullptr;
   mps_status rc = scratch_for(device, &scratch);
   if (rc != MPS_OK) return rc;

@@ -51,7 +51,7 @@ struct Slot {
   mps_state* st = nullptr;
   int frag = -1;
   Request* req = nullptr;
-  double* h_energy = nullptr;  // pinned
+  double* h_energy = nullptr;  // pinned: [0] the energy, [1] the state's StateFlags
   cudaEvent_t chunk_ev[2] = {nullptr, nullptr};
   int chunks_in_flight = 0;
   int chunk_head = 0;
@@ -220,6 +220,9 @@ void worker_loop(mps_server* s) {
         if (rc == MPS_OK) {
           cudaError_t e = cudaMemcpyAsync(sl.h_energy, sl.st->d_energy, sizeof(double), cudaMemcpyDeviceToHost,
                                           sl.ctx->stream);
+          if (e == cudaSuccess)  // the status flags land in the second half of the pinned buffer
+            e = cudaMemcpyAsync(sl.h_energy + 1, &sl.st->d_rep->not_converged, sizeof(StateFlags),
+                                cudaMemcpyDeviceToHost, sl.ctx->stream);
           if (e != cudaSuccess) rc = cuda_fail(e, "serving: energy read-back");
         }
         if (rc == MPS_OK) {
@@ -239,7 +242,8 @@ void worker_loop(mps_server* s) {
         Fragment& fm = s->frags[r->frag];
         fm.est_bytes = std::max<size_t>(sl.ctx->allocated, 1);  // measured footprint from now on
         r->energy = *sl.h_energy;
-        r->status = MPS_OK;
+        r->status = flags_status(*reinterpret_cast<const StateFlags*>(sl.h_energy + 1), true);
+        if (r->status != MPS_OK) r->error = last_error();
         r->phase = kDone;
         r->latency_ms = std::chrono::duration<double, std::milli>(Clock::now() - r->t_submit).count();
         sl.req = nullptr;
@@ -277,7 +281,7 @@ mps_status mps_server_create(int device, int32_t max_slots, size_t hbm_budget_by
     if (rc == MPS_OK) rc = mps_ctx_create(device, nullptr, &sl.ctx);
     if (rc == MPS_OK) {
       DeviceGuard guard(device);
-      cudaError_t e = cudaMallocHost(&sl.h_energy, sizeof(double));
+      cudaError_t e = cudaMallocHost(&sl.h_energy, 2 * sizeof(double));  // energy, then StateFlags
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.chunk_ev[0], cudaEventDisableTiming);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.chunk_ev[1], cudaEventDisableTiming);
       if (e != cudaSuccess) rc = cuda_fail(e, "mps_server_create");

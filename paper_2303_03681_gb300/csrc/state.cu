@@ -397,6 +397,7 @@ mps_status state_reset(mps_state* st, const uint8_t* bits) {
                                                     st->d_lam_off, st->d_chi, st->d_bits, st->n, st->d_rep);
   MPSV_CUDA(cudaGetLastError());
   st->broken = false;
+  st->nc_seen = 0;
   return MPS_OK;
 }
 
@@ -832,7 +833,18 @@ mps_status mps_apply_gates(mps_state* st, const mps_gate* gates, size_t n, mps_r
     st->broken = true;
     return cuda_fail(e, "mps_apply_gates");
   }
-  if (report) return mps_get_report(st, report);
+  mps_report r;
+  mps_status rc = mps_get_report(st, &r);
+  if (rc != MPS_OK) return rc;
+  if (report) *report = r;
+  // SVDs that reached the sweep cap since the host last looked (reset clears the count)
+  const int fresh = r.svd_not_converged - st->nc_seen;
+  st->nc_seen = r.svd_not_converged;
+  if (fresh > 0) {
+    set_error("mps_apply_gates: %d truncation SVDs reached the Jacobi sweep cap; their results were used as they stand",
+              fresh);
+    return MPS_ENOTCONV;
+  }
   return MPS_OK;
 }
 

@@ -72,7 +72,7 @@ __device__ __forceinline__ void warp_sum4(S& a, S& b, S& c, S& d) {
 // entries use the first m (A) rows.
 template <typename S>
 __device__ __forceinline__ int jacobi_pair_smem(cplx<S>* ai, cplx<S>* aj, int m, int len, int lane, S tol, S floor,
-                                                S tiny, S tau2) {
+                                                S tiny) {
   using C = cplx<S>;
   S alpha = 0, beta = 0, gr = 0, gi = 0;
   for (int r = lane; r < m; r += 32) {
@@ -85,7 +85,7 @@ __device__ __forceinline__ int jacobi_pair_smem(cplx<S>* ai, cplx<S>* aj, int m,
   warp_sum4(alpha, beta, gr, gi);
   S c;
   C sph;
-  if (!jacobi_rotation(alpha, beta, gr, gi, tol, floor, tiny, tau2, c, sph)) return 0;
+  if (!jacobi_rotation(alpha, beta, gr, gi, tol, floor, tiny, c, sph)) return 0;
   for (int r = lane; r < len; r += 32) {
     const C x = ai[r], y = aj[r];
     ai[r] = csub(cmk<S>(c * x.x, c * x.y), cmulc(sph, y));
@@ -97,7 +97,7 @@ __device__ __forceinline__ int jacobi_pair_smem(cplx<S>* ai, cplx<S>* aj, int m,
 // Same with the first column in registers: x[i] is row lane + 32 i.
 template <typename S>
 __device__ __forceinline__ int jacobi_pair_reg(cplx<S> (&x)[kClusterRegs], cplx<S>* aj, int m, int len, int lane,
-                                               S tol, S floor, S tiny, S tau2) {
+                                               S tol, S floor, S tiny) {
   using C = cplx<S>;
   S alpha = 0, beta = 0, gr = 0, gi = 0;
 #pragma unroll
@@ -114,7 +114,7 @@ __device__ __forceinline__ int jacobi_pair_reg(cplx<S> (&x)[kClusterRegs], cplx<
   warp_sum4(alpha, beta, gr, gi);
   S c;
   C sph;
-  if (!jacobi_rotation(alpha, beta, gr, gi, tol, floor, tiny, tau2, c, sph)) return 0;
+  if (!jacobi_rotation(alpha, beta, gr, gi, tol, floor, tiny, c, sph)) return 0;
 #pragma unroll
   for (int i = 0; i < kClusterRegs; ++i) {
     const int r = lane + 32 * i;
@@ -158,6 +158,17 @@ struct ClusterGeom {
   bool member;  // me < P
 };
 
+// Column id (0 .. ncols_pad-1) of column c of the block in slot `slot` of
+// CTA `me` in round `rnd` of a sweep: the block at position pos >= 1 has
+// moved rnd places along the circle 1 .. 2P-1 since the sweep began, when
+// position p held block p; position 0 keeps block 0.
+__device__ __forceinline__ int col_id(const ClusterGeom& g, int slot, int c, int rnd) {
+  const int pos = slot == 0 ? g.me : 2 * g.P - 1 - g.me;
+  const int M = 2 * g.P - 1;
+  const int blk = pos == 0 ? 0 : 1 + ((pos - 1 - rnd) % M + M) % M;
+  return blk * g.b + c;
+}
+
 // Stacked columns of one precision: shared-memory ping-pong slots
 // [pp][slot][c][len], or 2P global blocks [block][c][len] that stay put while
 // the round robin renames positions.
@@ -184,21 +195,43 @@ struct ColStore {
 // sweep rotates no pair (or max_sweeps); kOp 1: max_sweeps orthonormalisation
 // sweeps.  Every CTA of the cluster calls it (non-members only keep the
 // cluster barriers in step).  Returns the sweeps run.
+//
+// Tail rule (kOp 0): at the start of each sweep every CTA learns the squared
+// norms of all columns (nrm2, through distributed shared memory) and marks
+// the columns the truncation discards (truncation_tail, into tail[]); a pair
+// of two marked columns is not rotated.
 template <typename T, int kOp, bool kGlobal>
 __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColStore<T, kGlobal>& cs, int& cur, int max_sweeps, T tol, T floor,
-                              T tiny, T tau2, bool& converged, const cg::cluster_group& cluster, int* s_flag_in,
-                              int* s_any) {
+                              T tiny, double trunc_rel, int chi_max, double* nrm2, int* tail, bool& converged,
+                              const cg::cluster_group& cluster, int* s_flag_in, int* s_any) {
   using C = cplx<T>;
   // In the cross rounds, when every warp has one top-slot column, warp w
   // keeps it in registers for the b rotations it takes part in; only the
   // bottom-slot columns are re-read, so one barrier per sub-round orders
   // their hand-off.
   const bool cache_x = kOp == 0 && g.len <= 32 * kClusterRegs && g.b <= g.nw;
+  const T loose = T(2.0 / g.ncols);  // the tail rule's loose tolerance (pair_tol)
   const bool active = g.member && g.wp < g.b;
   int sweep = 0;
   converged = false;
   for (; sweep < max_sweeps; ++sweep) {
     int rotated = 0;
+    if (kOp == 0) {
+      // squared norms of this CTA's columns (positions hold their own blocks
+      // at the start of a sweep) to every member CTA
+      for (int c = g.wp; g.member && c < 2 * g.b; c += g.nw) {
+        const C* a = cs.col(cur, c / g.b, c % g.b, 0);
+        double acc = 0.0;
+        for (int r = g.wl; r < g.m; r += 32) acc += double(a[r].x) * a[r].x + double(a[r].y) * a[r].y;
+        acc = warp_sum(acc);
+        if (g.wl == 0) {
+          const int id = col_id(g, c / g.b, c % g.b, 0);
+          for (int r2 = 0; r2 < g.P; ++r2) *cluster.map_shared_rank(nrm2 + id, r2) = acc;
+        }
+      }
+      cluster.sync();
+      if (g.member) truncation_tail(nrm2, g.ncols_pad, trunc_rel, chi_max, tail);
+    }
     for (int rnd = 0; rnd < 2 * g.P - 1; ++rnd) {
       if (!g.member) {
         // not taking part: only the cluster barrier below
@@ -217,9 +250,11 @@ __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColSto
             }
             C* x = cs.col(cur, a0 / g.b, a0 % g.b, rnd);
             C* y = cs.col(cur, a1 / g.b, a1 % g.b, rnd);
-            if (kOp == 0)
-              rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tol, floor, tiny, tau2);
-            else
+            if (kOp == 0) {
+              const T tl = pair_tol(tail[col_id(g, a0 / g.b, a0 % g.b, rnd)], tail[col_id(g, a1 / g.b, a1 % g.b, rnd)],
+                                    tol, loose);
+              if (tl >= T(0)) rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tl, floor, tiny);
+            } else
               orth_pair<T>(x, y, g.m, g.len, g.wl);
           }
           __syncthreads();
@@ -236,16 +271,22 @@ __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColSto
         }
         for (int sr = 0; sr < g.b; ++sr) {
           if (cache_x) {
-            if (active)
-              rotated |= jacobi_pair_reg<T>(xr, cs.col(cur, 1, (g.wp + sr) % g.b, rnd), g.m, g.len, g.wl, tol,
-                                            floor, tiny, tau2);
+            if (active) {
+              const T tl = pair_tol(tail[col_id(g, 0, g.wp, rnd)], tail[col_id(g, 1, (g.wp + sr) % g.b, rnd)], tol,
+                                    loose);
+              if (tl >= T(0))
+                rotated |= jacobi_pair_reg<T>(xr, cs.col(cur, 1, (g.wp + sr) % g.b, rnd), g.m, g.len, g.wl, tl,
+                                              floor, tiny);
+            }
           } else {
             for (int pw = g.wp; pw < g.b; pw += g.nw) {
               C* x = cs.col(cur, 0, pw, rnd);
               C* y = cs.col(cur, 1, (pw + sr) % g.b, rnd);
-              if (kOp == 0)
-                rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tol, floor, tiny, tau2);
-              else
+              if (kOp == 0) {
+                const T tl = pair_tol(tail[col_id(g, 0, pw, rnd)], tail[col_id(g, 1, (pw + sr) % g.b, rnd)], tol,
+                                      loose);
+                if (tl >= T(0)) rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tl, floor, tiny);
+              } else
                 orth_pair<T>(x, y, g.m, g.len, g.wl);
             }
           }
@@ -344,7 +385,7 @@ __device__ __forceinline__ void svd_cluster_body(const ClusterGeom& g, const cg:
                                                  double& s_nrm, int* s_any, long long t_start) {
   using C = cplx<S>;
   long long t_load = 0, t_lo = 0, t_fix = 0;
-  const bool mixed = sizeof(S) == 8 && sizeof(R) == 4 && p.mixed;
+  const bool mixed = sizeof(S) == 8 && p.mixed;
   const int m = g.m, ncols = g.ncols, len = g.len, b = g.b, P = g.P, me = g.me, nt = g.nt;
   const ClusterSvdSmem<S> L(b, kGlobal ? 0 : len, g.ncols_pad, nt);
   double* sig = reinterpret_cast<double*>(smem + L.sig);
@@ -406,8 +447,10 @@ __device__ __forceinline__ void svd_cluster_body(const ClusterGeom& g, const cg:
   // product); columns with squared norm below (4 u ||A||_F)^2 are rounding
   // noise and left alone.
   const double tol_scale = 4.0 * sqrt(double(max(m, ncols)));
-  // pairs of columns that end up below the truncation threshold together need no rotation
-  const double tau2 = p.trunc_rel * p.trunc_rel * fro2 / (double(ncols) * double(ncols));
+  // the tail rule's per-sweep scratch: squared norms and tail flags of all
+  // columns (the singular values and ranks use the same arrays afterwards)
+  double* nrm2 = sig;
+  int* tail = rnk;
   int cur = 0, used = 0, used32 = 0;
   bool converged = false;
   t_load = clock64();
@@ -417,8 +460,8 @@ __device__ __forceinline__ void svd_cluster_body(const ClusterGeom& g, const cg:
     int cur32 = 0;
     bool conv32 = false;
     used32 = cluster_sweeps<float, 0, kGlobal>(g, cs32, cur32, p.max_sweeps, float(tol_scale) * u32,
-                                      float(16.0 * double(u32) * double(u32) * fro2), 1e-35f, float(tau2), conv32,
-                                      cluster, s_flag_in, s_any);
+                                               float(16.0 * double(u32) * double(u32) * fro2), 1e-35f, p.trunc_rel,
+                                               p.chi_max, nrm2, tail, conv32, cluster, s_flag_in, s_any);
     used = used32;
     t_lo = clock64();
     // FP64 columns: V promoted (A follows from the theta below)
@@ -432,19 +475,24 @@ __device__ __forceinline__ void svd_cluster_body(const ClusterGeom& g, const cg:
     // every CTA has read its FP32 columns before the first hand-over may
     // overwrite them (in shared memory they share a buffer with FP64 ones)
     cluster.sync();
-    bool dummy;
-    cluster_sweeps<S, 1, kGlobal>(g, cs, cur, 1, S(0), S(0), S(0), S(0), dummy, cluster, s_flag_in, s_any);
-    // the diagonal of the first-order step: |v|^2 -> 1
-    for (int c = g.wp; g.member && c < 2 * b; c += g.nw) {
-      C* v = cs.col(cur, c / b, c % b, 0);
-      S n2 = 0;
-      for (int r = m + g.wl; r < len; r += 32) n2 = fma(v[r].x, v[r].x, fma(v[r].y, v[r].y, n2));
-      n2 = warp_sum(n2);
-      const S f = S(1.5) - S(0.5) * n2;
-      if (n2 > S(0))
-        for (int r = m + g.wl; r < len; r += 32) v[r] = cmk<S>(f * v[r].x, f * v[r].y);
+    // two first-order passes: E ~ 1e-6 -> E^2 -> E^4 (one pass left V
+    // unitary only to ~1e-10 after long FP32 phases)
+    for (int pass = 0; pass < 2; ++pass) {
+      bool dummy;
+      cluster_sweeps<S, 1, kGlobal>(g, cs, cur, 1, S(0), S(0), S(0), 0.0, 0, nrm2, tail, dummy, cluster, s_flag_in,
+                                    s_any);
+      // the diagonal of the first-order step: |v|^2 -> 1
+      for (int c = g.wp; g.member && c < 2 * b; c += g.nw) {
+        C* v = cs.col(cur, c / b, c % b, 0);
+        S n2 = 0;
+        for (int r = m + g.wl; r < len; r += 32) n2 = fma(v[r].x, v[r].x, fma(v[r].y, v[r].y, n2));
+        n2 = warp_sum(n2);
+        const S f = S(1.5) - S(0.5) * n2;
+        if (n2 > S(0))
+          for (int r = m + g.wl; r < len; r += 32) v[r] = cmk<S>(f * v[r].x, f * v[r].y);
+      }
+      __syncthreads();
     }
-    __syncthreads();
     // A = C~ V in FP64 for this CTA's columns
     for (size_t t = threadIdx.x; g.member && t < (size_t)2 * b * m; t += nt) {
       const int c = (int)(t / m), r = (int)(t % m);
@@ -467,8 +515,8 @@ __device__ __forceinline__ void svd_cluster_body(const ClusterGeom& g, const cg:
   const S tol = p.tol > 0 ? S(p.tol) : S(tol_scale) * eps_u;
   const S floor = S(16.0 * double(eps_u) * double(eps_u) * fro2);
   const S tiny = sizeof(S) == 8 ? S(1e-290) : S(1e-35f);
-  used += cluster_sweeps<S, 0, kGlobal>(g, cs, cur, p.max_sweeps, tol, floor, tiny, S(tau2), converged, cluster, s_flag_in,
-                               s_any);
+  used += cluster_sweeps<S, 0, kGlobal>(g, cs, cur, p.max_sweeps, tol, floor, tiny, p.trunc_rel, p.chi_max, nrm2, tail,
+                                        converged, cluster, s_flag_in, s_any);
   const int sweep = used;
 
   // ---- singular values: norms of the A parts, shared with every CTA
