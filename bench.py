@@ -36,6 +36,8 @@ from paper_2303_03681_gb300.inputs import (MASTER_SEED, brickwork_circuit, hf_bi
 from paper_2303_03681_gb300.inputs.circuits import CircuitTemplate, uccsd_excitations  # noqa: E402
 
 METRIC = "energy evals/s"
+# accuracy target of an energy against the FP64 oracle (Ha)
+ENERGY_TOL_HA = 1e-6
 # derived ALU peaks (152 SMs x 2070 MHz): FP32 128 FMA/clk/SM, FP64 2 FMA/clk/SM
 SM_COUNT, SM_MHZ = 152, 2070.0
 ALU_PEAK_TFLOPS = {"f32": SM_COUNT * 128 * 2 * SM_MHZ * 1e6 / 1e12, "f64": SM_COUNT * 2 * 2 * SM_MHZ * 1e6 / 1e12}
@@ -58,7 +60,7 @@ def build_workload(name, args, rank):
                     hamiltonian="JW of random 25-orbital integrals, h~N(0,1), (pq|rs)~N(0,0.1^2) 8-fold",
                     theta="U[-0.05, 0.05] per excitation, new draw per step")
         return dict(ham=ham, tmpl=tmpl, bits=bits, chi=chi, trunc=args.trunc_rel, theta_scale=0.05,
-                    precision=args.precision or "fp32", desc=desc)
+                    precision=args.precision or "fp64", desc=desc)
     if name == "c1":
         h, g = random_integrals(6, make_rng(MASTER_SEED))
         ham = jw_molecular_hamiltonian(h, g)
@@ -348,7 +350,8 @@ def run_gpu(args):
         t0 = time.perf_counter()
         e, status = mps.vqe_eval_batch([(states[b], C, H, host_thetas[k * B + b], w["bits"]) for b in range(B)])
         e2e_times.append(time.perf_counter() - t0)
-        assert all(s == 0 for s in status), status
+        # MPS_ENOTCONV still delivers the energy; it is counted in last_step_report
+        assert all(s in (0, mps.MPS_ENOTCONV) for s in status), status
     e2e_s = max_over_ranks(sum(e2e_times), dist, dev)
 
     if rank != 0:
@@ -388,15 +391,14 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64" if w["precision"] == "fp32" else "c128",
         "data": "synthetic",
-        "config": dict(w["desc"], precision=(f"{w['precision']} storage/contractions, "
+        "config": dict(w["desc"], precision=({"fp32": "complex64", "fp64": "complex128"}[w["precision"]]
+                                             + " storage and contractions, "
                                              + {"fp32": "FP32 Jacobi SVD",
-                                                "fp64": ("FP64-accurate Jacobi SVD (FP32 sweeps, FP64 re-orthonormalisation,"
-                                                         " FP64 sweeps)" if w["precision"] == "fp32" else
-                                                         "FP64 Jacobi SVD"),
+                                                "fp64": ("FP64-accurate Jacobi SVD (FP32 sweeps, FP64 "
+                                                         "re-orthonormalisation, FP64 sweeps)"),
                                                 "fp64-all": "FP64 Jacobi SVD"}[args.svd]
                                              + ", FP64 energy sum"),
-                       contractions=("tcgen05 TF32 hi/lo split, 4 products" if args.tensor_cores and w["precision"] == "fp32"
-                                     else "CUDA cores"),
+                       contractions=contraction_label(args, w, reps),
                        batch=f"{B} concurrent evaluations per step (one stream each)",
                        l2="flushed between steps (256 MB write)", parallelism=f"replicas x{world}"),
         "e2e": {"value": job_throughput(args.steps * B, world, e2e_s), "unit": "evals/s",
@@ -461,6 +463,19 @@ def serve_phase(mps, device, C, H, w, args, rate):
             "hbm_peak_bytes": st["peak_bytes"]}
 
 
+def contraction_label(args, w, reps):
+    """What ran the environment contractions in the timed steps: the
+    tensor-core path serves complex64 states at bond dimension >= 64 only."""
+    if w["precision"] != "fp32":
+        return "CUDA cores (FP64)"
+    if not args.tensor_cores:
+        return "CUDA cores (FP32)"
+    top = max(r["max_chi"] for r in reps)
+    if top < 64:
+        return f"CUDA cores (FP32); tcgen05 enabled but unused (bond dimension {top} < 64)"
+    return "tcgen05 TF32 hi/lo split, 4 products, at bond dimension >= 64; CUDA cores (FP32) below"
+
+
 def oracle_check(mps, state, C, H, w, trunc_rel):
     """|E_gpu - E_oracle| for this workload at the reference angles of a
     stored oracle energy (tests/golden/*_oracle.json, written by a committed
@@ -474,12 +489,15 @@ def oracle_check(mps, state, C, H, w, trunc_rel):
         lo, hi = rec["theta_range"]
         theta = make_rng(rec["theta_seed"]).uniform(lo, hi, w["tmpl"].n_params)
         e, status = mps.vqe_eval_batch([(state, C, H, theta, w["bits"])])
-        if status[0] != 0:
+        if status[0] not in (0, mps.MPS_ENOTCONV):
             return {"error": f"status {int(status[0])}"}
+        err = abs(float(e[0]) - rec["oracle_energy"])
+        rep = state.report()
         return {"reference": os.path.relpath(path, ROOT), "theta_seed": rec["theta_seed"],
                 "energy_gpu": float(e[0]), "energy_oracle": rec["oracle_energy"],
-                "abs_error_ha": abs(float(e[0]) - rec["oracle_energy"]),
-                "discarded_weight_gpu": state.report()["discarded_weight"],
+                "abs_error_ha": err, "tolerance_ha": ENERGY_TOL_HA, "within_tol": bool(err <= ENERGY_TOL_HA),
+                "svd_not_converged": int(rep["svd_not_converged"]),
+                "discarded_weight_gpu": rep["discarded_weight"],
                 "discarded_weight_oracle": rec["oracle_discarded_weight"]}
     return None
 

@@ -42,6 +42,8 @@ def test_bench_oracle_check_matches_its_record():
     seen = []
 
     class FakeMps:
+        MPS_ENOTCONV = 5
+
         @staticmethod
         def vqe_eval_batch(reqs):
             seen.append(reqs)
@@ -49,10 +51,11 @@ def test_bench_oracle_check_matches_its_record():
 
     class FakeState:
         def report(self):
-            return {"discarded_weight": 0.0}
+            return {"discarded_weight": 0.0, "svd_not_converged": 0}
 
     chk = bench.oracle_check(FakeMps, FakeState(), None, None, w, w["trunc"])
     assert chk["reference"] == os.path.join("tests", "golden", "c1_brickwork12_oracle.json")
     assert abs(chk["abs_error_ha"] - 2e-12) <= 1e-15 and chk["energy_oracle"] == rec["oracle_energy"]
+    assert chk["within_tol"] and chk["tolerance_ha"] == 1e-6
     assert len(seen) == 1 and seen[0][0][3].shape == (0,)  # C1 has no angles
     assert bench.oracle_check(FakeMps, FakeState(), None, None, w, 1e-3) is None  # other truncation: no record

@@ -1,10 +1,10 @@
-"""mps_gate2_noalloc against the regular gate path (GPU).
+"""mps_gate2_noalloc against the regular gate path and the oracle (GPU).
 
 mps_gate2_noalloc exists for callers that cannot allocate device memory; it
 applies one two-qubit gate to caller-owned device buffers using a fixed
 scratch array inside the library.  This test applies the same two gates in a
-row through it and through mps_apply_gates on an MPS with the same tensors,
-and compares the gauge-invariant results: the new bond's singular values and
+row through it and through mps_apply_gates on an MPS with the same tensors (and the FP64
+oracle's update of those tensors), and compares the gauge-invariant results: the new bond's singular values and
 the two-site tensor B~_q B~_{q+1}, within the complex128 parity tolerance of
 the other GPU tests (1e-10).  It runs last so that a failure here comes after
 every other test, and it passes alone in a fresh process too: the entry
@@ -16,6 +16,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from oracle import mps as orc
 from paper_2303_03681_gb300.inputs import brickwork_circuit, haar_su4, make_rng
 
 pytestmark = pytest.mark.gpu
@@ -55,6 +56,7 @@ def test_noalloc_gate_matches_mps_apply_gates():
     chi_out = torch.zeros(1, dtype=torch.int32, device=dev)
     fn = _noalloc(mps.library())
     stream = torch.cuda.current_stream().cuda_stream
+    ref = orc.MPS([b.copy() for b in B], [x.copy() for x in lam])
 
     for call in range(2):
         u = haar_su4(rng)
@@ -75,6 +77,12 @@ def test_noalloc_gate_matches_mps_apply_gates():
         theta_got = np.einsum("aim,mjb->aijb", got_l, got_r)
         theta_ref = np.einsum("aim,mjb->aijb", Bref[q], Bref[q + 1])
         assert np.max(np.abs(theta_got - theta_ref)) <= 1e-10
+        # the FP64 oracle's Hastings update of the same tensors
+        orc.apply_2q(ref, q, u, chi_max, 0.0)
+        assert ref.B[q].shape[2] == k
+        assert np.allclose(lam_out[:k].cpu().numpy(), ref.lam[q + 1], rtol=0, atol=1e-10)
+        theta_orc = np.einsum("aim,mjb->aijb", ref.B[q], ref.B[q + 1])
+        assert np.max(np.abs(theta_got - theta_orc)) <= 1e-10
         chi_m = k  # the second call starts from the first call's output
 
 
@@ -87,3 +95,7 @@ def test_noalloc_rejects_sizes_beyond_the_scratch():
     rc = fn(0, None, 33, 2, 2, dummy, dummy, dummy, dummy, g.ctypes.data_as(ctypes.c_void_p), 8, 0.0, dummy)
     assert rc == mps.MPS_EINVAL
     assert b"1..32" in mps.library().mps_last_error()
+    # a device that does not exist is refused before anything is issued
+    rc = fn(63, None, 2, 2, 2, dummy, dummy, dummy, dummy, g.ctypes.data_as(ctypes.c_void_p), 8, 0.0, dummy)
+    assert rc == mps.MPS_EINVAL
+    assert b"no CUDA device 63" in mps.library().mps_last_error()
