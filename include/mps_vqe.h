@@ -55,10 +55,21 @@ typedef enum {
 } mps_status;
 
 /* Arithmetic of a state.  The truncation SVD and the energy sum are FP64 in
- * every mode unless mps_config.svd_fp64 = 0. */
+ * every mode unless mps_config.svd_fp64 = 0.  The split-product modes keep
+ * complex64 storage and run the theta contraction C = Q (B_q B_{q+1}) and
+ * B~_q = C V^dagger (Eqs. tildeC, Bl) as tensor-core GEMMs (tcgen05, operands
+ * loaded with TMA) in which every real operand value is split into two
+ * pieces and each real product is the sum of three piece products
+ * (hi*hi + hi*lo + lo*hi) accumulated in FP32; their environment
+ * contractions use the tensor cores at bond dimension >= 64 as
+ * mps_config.tensor_cores does. */
 typedef enum {
-  MPS_PREC_FP64 = 0,  /* complex128 storage, FP64 contractions */
-  MPS_PREC_FP32 = 1   /* complex64 storage, FP32 contractions */
+  MPS_PREC_FP64 = 0,   /* complex128 storage, FP64 contractions */
+  MPS_PREC_FP32 = 1,   /* complex64 storage, FP32 CUDA-core contractions */
+  MPS_PREC_BF16X3 = 2, /* complex64 storage, BF16 pieces (16 bits of each value kept) */
+  MPS_PREC_TF32X3 = 3, /* complex64 storage, TF32 pieces (22 bits kept: about FP32 accuracy) */
+  MPS_PREC_AUTO = 4    /* complex64 storage, TF32X3 where a bond capacity reaches 256, FP32
+                          CUDA cores below */
 } mps_precision;
 
 typedef struct {
@@ -193,6 +204,44 @@ void mps_destroy(mps_state* st);
  * asynchronous circuits before it; mps_reset clears the count) reached its
  * sweep cap: the gates are applied and the report is filled all the same. */
 mps_status mps_apply_gates(mps_state* st, const mps_gate* gates, size_t n, mps_report* report);
+
+/* The theta contraction of one two-qubit gate on its own (the G1 step of the
+ * Hastings update, Methods "MPS algorithm for quantum circuit simulation":
+ * C = Q (B_q B_{q+1}) before the lam scaling of Eq. tildeC), for complex64
+ * site tensors in device memory:
+ *   B_left   [chi_l][2][chi_m] complex64 (interleaved re, im floats);
+ *   B_right  [chi_m][2][chi_r] complex64;
+ *   gate     host array, 4x4 row-major complex (32 doubles), index 2 i_q + i_{q+1};
+ *   C_out    [(a_l, i)][(j, a_r)] = (2 chi_l) x (2 chi_r) complex64, row-major,
+ *            C_out[(2 a_l + i) * 2 chi_r + j chi_r + a_r].
+ * precision: MPS_PREC_FP32 (CUDA cores, FP32), MPS_PREC_TF32X3 or
+ * MPS_PREC_BF16X3 (the tensor-core split products mps_apply_gates uses for
+ * such states); others fail with MPS_EINVAL, as do bond dimensions outside
+ * 1..4096.  Work is issued on the context stream and the call returns without
+ * synchronising (the host arrays are copied before it returns); the context
+ * keeps a workspace sized for the largest call so far (released with the
+ * context).  The device arrays belong to the caller and must not overlap. */
+mps_status mps_contract_theta(mps_ctx* ctx, int32_t precision, int32_t chi_l, int32_t chi_m, int32_t chi_r,
+                              const void* B_left, const void* B_right, const double* gate, void* C_out);
+
+/* The truncation SVD of one theta on its own (the S1/S2 step of the Hastings
+ * update: one-sided Jacobi SVD of Algorithm 1, Methods "SVD and one-side
+ * jacobi", then the truncation rule of mps_apply_gates).  C is an m x n
+ * complex matrix in device memory, row-major (complex128 for MPS_PREC_FP64,
+ * complex64 for MPS_PREC_FP32); m and n must be even (m = 2 chi_l, n =
+ * 2 chi_r in the gate update) and in 2..4096.  The kept count k =
+ * min(chi_max, #{s_i > trunc_rel s_1}) >= 1 goes to *k_out (host); s_out
+ * (device, room for min(m, n) doubles) receives s_1 >= ... >= s_k, not
+ * renormalised; Vh_out (device, room for min(chi_max, m, n) x n entries of the
+ * input precision, row-major) the rows of V^H, i.e. the right singular
+ * vectors conjugated.  svd_fp64 as in mps_config.  `report` (nullable)
+ * receives the sweep counts and the discarded weight.  The context keeps a
+ * workspace sized for the largest call so far; the call synchronises its
+ * stream and returns MPS_ENOTCONV (results written) when the sweep cap was
+ * reached. */
+mps_status mps_truncated_svd(mps_ctx* ctx, int32_t precision, int32_t m, int32_t n, const void* C, int32_t chi_max,
+                             double trunc_rel, int32_t svd_fp64, double* s_out, void* Vh_out, int32_t* k_out,
+                             mps_report* report);
 
 /* Upload a circuit template (see mps_template_gate) with n_params angles. */
 mps_status mps_circuit_create(mps_ctx* ctx, int32_t n_qubits, const mps_template_gate* gates,

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmpsvqe.so")
-SOURCES = ["state.cu", "energy.cu", "noalloc.cu", "server.cu"]
+SOURCES = ["state.cu", "energy.cu", "noalloc.cu", "server.cu", "tc_gates.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-Xptxas", "-O3"]
@@ -60,7 +60,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
                 print(err, file=sys.stderr)
     if force or jobs or _newer(LIB, objs):
         tmp = LIB + ".tmp"
-        run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcuda", "-lpthread"])
+        run([nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
         os.replace(tmp, LIB)
     return LIB
 

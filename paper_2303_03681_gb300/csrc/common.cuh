@@ -197,16 +197,27 @@ __device__ __forceinline__ bool jacobi_rotation<double>(double alpha, double bet
 //    to the others, so the kept columns converge quickly (a bare per-column
 //    threshold did not: a column just above it never converged against mixed
 //    columns just below it).
-//  * kTailLoose otherwise, for D columns with nrm2 <= cut / 4: pairs of two
-//    of them are rotated only while |g| > loose_tol sqrt(b_ii b_jj) with
-//    loose_tol = 2 / n.  By Gershgorin on their Gram matrix the singular
-//    values of that block then stay below (cut / 4)(1 + n loose_tol) < cut.
+//  * kTailLoose otherwise, for the deep tail T: the D columns with nrm2 <=
+//    t_d, where t_d <= cut / 4 is the largest such norm below a gap, i.e.
+//    the next larger nrm2 of any column is at least 4 t_d.  Pairs of two of
+//    them are rotated only while |g| > loose_tol sqrt(b_ii b_jj), loose_tol =
+//    min(2 / n, cut / (16 sum_T nrm2)), returned in *loose.  By Gershgorin on
+//    their Gram matrix the singular values of T then stay below
+//    (cut / 4)(1 + n loose_tol) < cut.  Every other column has nrm2 >= 4
+//    t_d, so its rotations against T have small angles (|s| <= 4|g| / (3
+//    nrm2)) and disturb its orthogonality to the rest of T by at most
+//    loose_tol sum_T nrm2 / nrm2 <= 1/4 of what it was: it still converges.
+//    (Without the gap a degenerate pair of columns straddling the threshold
+//    rotated by large angles and carried the loose couplings of its deep
+//    member into its tight one, and with 2 / n alone columns just above the
+//    threshold crawled against many mixed columns just below it.)
 //  * 0 for every other column (the normal stopping rule).
 // Every thread of the block calls it; blocks with the same nrm2 and size
 // compute the same classes.
 constexpr int kTailLoose = 1, kTailSkip = 2;
 
-__device__ __forceinline__ void truncation_tail(const double* nrm2, int n, double trunc_rel, int chi_max, int* cls) {
+__device__ __forceinline__ void truncation_tail(const double* nrm2, int n, double trunc_rel, int chi_max, int* cls,
+                                                double* loose) {
   __shared__ double s_red[33];
   __shared__ int s_cnt;
   __shared__ double s_cut;
@@ -264,8 +275,49 @@ __device__ __forceinline__ void truncation_tail(const double* nrm2, int n, doubl
   __syncthreads();
   const double cut = s_cut;
   const bool skip = s_red[32] <= 0.25 * cut;
+  // deep-tail threshold t_d: the largest candidate norm (a discarded column
+  // with nrm2 <= cut / 4) whose next larger norm among all columns is at
+  // least 4 times it
+  double td = -1.0;
+  if (!skip)
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+      const double v = nrm2[c];
+      if (cls[c] || !(v <= 0.25 * cut)) continue;
+      double nxt = INFINITY;
+      for (int h = 0; h < n; ++h)
+        if (nrm2[h] > v) nxt = fmin(nxt, nrm2[h]);
+      if (nxt >= 4.0 * v) td = fmax(td, v);
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) td = fmax(td, __shfl_xor_sync(0xffffffffu, td, o));
+  __syncthreads();
+  if (lane == 0) s_red[warp] = td;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = -1.0;
+    for (int w = 0; w < nw; ++w) v = fmax(v, s_red[w]);
+    s_red[32] = v;
+  }
+  __syncthreads();
+  td = s_red[32];
   for (int c = threadIdx.x; c < n; c += blockDim.x)
-    cls[c] = cls[c] ? 0 : (skip ? kTailSkip : (nrm2[c] <= 0.25 * cut ? kTailLoose : 0));
+    cls[c] = cls[c] ? 0 : (skip ? kTailSkip : (nrm2[c] <= td ? kTailLoose : 0));
+  __syncthreads();
+  // weight of the deep tail T, summed in a fixed order, for the loose tolerance
+  part = 0.0;
+  for (int c = threadIdx.x; c < n; c += blockDim.x)
+    if (cls[c] == kTailLoose) part += nrm2[c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  __syncthreads();
+  if (lane == 0) s_red[warp] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < nw; ++w) v += s_red[w];
+    const double l = 2.0 / n;
+    *loose = v > 0.0 ? fmin(l, cut / (16.0 * v)) : l;
+  }
   __syncthreads();
 }
 

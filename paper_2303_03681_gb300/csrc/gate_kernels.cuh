@@ -180,7 +180,9 @@ __device__ int jacobi_sweeps(cplx<S>* A, cplx<S>* V, int m, int n, int max_sweep
       if (lane == 0) nrm2[j] = acc;
     }
     __syncthreads();
-    truncation_tail(nrm2, n, trunc_rel, chi_max, tail);
+    __shared__ double s_loose;
+    truncation_tail(nrm2, n, trunc_rel, chi_max, tail, &s_loose);
+    const S loose = S(s_loose);
     if (threadIdx.x == 0) *s_flag = 0;
     __syncthreads();
     bool rotated = false;
@@ -189,7 +191,7 @@ __device__ int jacobi_sweeps(cplx<S>* A, cplx<S>* V, int m, int n, int max_sweep
         int i, j;
         rr_pair(r, k, nn, i, j);
         if (j >= n) continue;
-        const S tl = pair_tol(tail[i], tail[j], tol, S(2.0 / n));
+        const S tl = pair_tol(tail[i], tail[j], tol, loose);
         if (tl < S(0)) continue;
         C* ai = A + (size_t)i * m;
         C* aj = A + (size_t)j * m;

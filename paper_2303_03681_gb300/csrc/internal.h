@@ -1,6 +1,7 @@
 // Host-side objects behind the opaque handles of mps_vqe.h.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -58,6 +59,13 @@ struct CircuitGraph {
 
 }  // namespace mpsv
 
+namespace mpsv {
+struct ContractWork;
+void contract_work_free(mps_ctx* ctx);
+struct SvdWork;
+void svd_work_free(mps_ctx* ctx);
+}  // namespace mpsv
+
 struct mps_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -78,6 +86,8 @@ struct mps_ctx {
   std::vector<cudaEvent_t> pool;
   bool use_graphs = true;                           // replay circuits as CUDA graphs (mps_ctx_set_graphs)
   mpsv::CircuitGraph* capturing = nullptr;          // graph being captured on this context's stream
+  mpsv::ContractWork* contract = nullptr;           // workspace of mps_contract_theta
+  mpsv::SvdWork* svdw = nullptr;                     // workspace of mps_truncated_svd
   std::vector<mpsv::CircuitGraph*> graph_watch;     // graphs replayed since the last profile collection
 };
 
@@ -95,6 +105,17 @@ struct KernelScope {
 namespace mpsv {
 mps_status dev_alloc(mps_ctx* ctx, void** p, size_t bytes);
 void dev_free(mps_ctx* ctx, void* p);
+}  // namespace mpsv
+
+namespace mpsv {
+// Workspace of the tensor-core gate contractions (tc_gates.cu): the hi / lo
+// operand planes (A_hi, A_lo, B_hi, B_lo; K-major, ld elements per row) and
+// their TMA tensor maps, sized once for the state's largest bond capacity.
+struct TcWork {
+  void* planes[4] = {nullptr, nullptr, nullptr, nullptr};
+  CUtensorMap maps[4];
+  int ld = 0, rows_a = 0, rows_b = 0;
+};
 }  // namespace mpsv
 
 struct mps_state {
@@ -124,6 +145,10 @@ struct mps_state {
   std::vector<uint8_t> last_bits;
   bool broken = false;
   int nc_seen = 0;  // svd_not_converged as last read by the host (mps_apply_gates)
+  // split-product tensor-core gate contractions: 0 (CUDA cores) or the
+  // mps_precision that selected them (TF32X3, BF16X3, AUTO)
+  int tc_gates = 0;
+  mpsv::TcWork* tcw = nullptr;
   // circuit binding workspace (per state, so states sharing a circuit can run concurrently)
   mpsv::DevGate* d_bound = nullptr;
   size_t bound_cap = 0;
@@ -206,4 +231,10 @@ mps_status state_run_circuit(mps_state* st, const mps_circuit* c, const double* 
 void graph_destroy(mps_ctx* ctx, CircuitGraph* g);
 // energy.cu
 mps_status ham_energy_async(mps_state* st, mps_ham* h, double* d_out);
+// tc_gates.cu
+mps_status tc_gates_setup(mps_state* st);
+void tc_gates_free(mps_state* st);
+bool tc_gates_used(const mps_state* st, int q);  // this bond's gates take the tensor-core contractions
+void tc_theta(mps_state* st, const DevGate* g, int q, cudaStream_t s);
+void tc_g3(mps_state* st, int q, cudaStream_t s);
 }  // namespace mpsv

@@ -95,7 +95,7 @@ size_t slots_bytes(const mps_server* s) {
 size_t estimate_bytes(const Fragment& f) {
   const int n = f.ham->n;
   const int chi = f.cfg.chi_max;
-  const size_t elem = f.cfg.precision == MPS_PREC_FP32 ? 8 : 16;
+  const size_t elem = f.cfg.precision == MPS_PREC_FP64 ? 16 : 8;
   auto cap = [&](int b) {
     const int e = std::min(b, n - b);
     return e >= 30 ? chi : std::min(chi, 1 << e);
@@ -109,8 +109,16 @@ size_t estimate_bytes(const Fragment& f) {
     const size_t cl = cap(j), cr = cap(j + 1);
     env = std::max(env, 2 * (size_t)L.n_children * cr * cr * elem + (size_t)L.n_parents * 2 * cl * cr * elem);
   }
+  // the operand planes of the split-product tensor-core contractions: A and B
+  // pieces of (2 and 4) x maxcap rows by 4 maxcap FP32 values, hi and lo
+  size_t tc = 0;
+  if (f.cfg.precision != MPS_PREC_FP64 && f.cfg.precision != MPS_PREC_FP32) {
+    int maxcap = 1;
+    for (int b = 0; b <= n; ++b) maxcap = std::max(maxcap, cap(b));
+    tc = 2 * (size_t)6 * (maxcap + 64) * (4 * (size_t)maxcap + 64) * 4;
+  }
   return sites * elem + 3 * mn * 16 + (size_t)f.circ->n_gates * sizeof(DevGate) + env +
-         (size_t)f.ham->n_terms * sizeof(double) + (1 << 20);
+         (size_t)f.ham->n_terms * sizeof(double) + tc + (1 << 20);
 }
 
 void fail(mps_server* s, Slot& sl, mps_status rc) {
@@ -313,8 +321,8 @@ mps_status mps_server_add_fragment(mps_server* srv, const mps_circuit* circuit, 
               circuit->n, ham->n);
     return MPS_EINVAL;
   }
-  if (cfg->chi_max < 1 || cfg->chi_max > 1024 || (cfg->precision != MPS_PREC_FP64 && cfg->precision != MPS_PREC_FP32)) {
-    set_error("mps_server_add_fragment: invalid mps_config");
+  if (cfg->chi_max < 1 || cfg->chi_max > 1024 || cfg->precision < MPS_PREC_FP64 || cfg->precision > MPS_PREC_AUTO) {
+    set_error("mps_server_add_fragment: invalid mps_config (chi_max %d, precision %d)", cfg->chi_max, cfg->precision);
     return MPS_EINVAL;
   }
   Fragment f;

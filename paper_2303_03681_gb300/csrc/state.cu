@@ -247,7 +247,11 @@ template <typename S, typename R> static SvdPlan cluster_svd_plan(int mcap, int 
     }
     return pl;
   } else {
-  for (int P = ncap < 64 ? 4 : ((ncap >= 192 && max16 > 0) ? 16 : 8); P <= 16; P *= 2) {
+  // FP64 sweeps: at most 8 CTAs of up to 8 warps (one column pair each), so
+  // that a block holds enough pairs to keep its SM's FP64 units busy; with
+  // many evaluations in flight, 16 CTAs of 4 busy warps left most SMs waiting
+  // at cluster barriers (0.47 against 0.70 evaluations/s at 32 streams)
+  for (int P = ncap < 64 ? 4 : 8; P <= 8; P *= 2) {
     if (P == 16 && max16 <= 0) break;
     const int b = (ncap + 2 * P - 1) / (2 * P);
     ClusterSvdSmem<S> L(b, mcap + ncap, 2 * P * b, 32 * b);
@@ -258,14 +262,52 @@ template <typename S, typename R> static SvdPlan cluster_svd_plan(int mcap, int 
       return pl;
     }
   }
-  const int P = max16 > 0 ? 16 : 8;
+  // columns too long for shared memory at the capacity: a global workspace,
+  // and the whole shared memory of the CTA so that the actual sizes use it
+  // whenever they fit
+  const int P = 8;
   const int b = (ncap + 2 * P - 1) / (2 * P);
   pl.P = P;
   pl.threads = std::min(32 * b, kClusterMaxThreads<S>);
   pl.global = true;
-  pl.smem = std::min(lim, std::max(ClusterSvdSmem<S>(b, 0, 2 * P * b, pl.threads).total, (size_t)96 * 1024));
+  pl.smem = lim;
   return pl;
   }
+}
+
+// The truncation SVD of one theta (bond capacities mcap x ncap): the
+// cluster kernel when the plan has CTAs (it reads the row-major C and the
+// lam_l row weights itself; gbuf is its global workspace), else the
+// single-CTA kernel on the column-major lam-scaled copy A with the V
+// workspace.  Writes B~_{q+1} = V^H rows, lam_{q+1}, chi[q+1] and the report.
+template <typename R, typename S>
+static void launch_svd(mps_ctx* ctx, const SvdPlan& plan, int mcap, int ncap, const SvdParams& p,
+                       const cplx<R>* Cm, cplx<S>* A, cplx<S>* V, const double* lam_l, int* chi, int q,
+                       cplx<R>* Bnext, double* lam_next, DevReport* rep, cudaStream_t s) {
+  KernelScope k(ctx, MPS_K_SVD);
+  if (plan.P) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(plan.P);
+    cfg.blockDim = dim3(plan.threads);
+    cfg.dynamicSmemBytes = plan.smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = plan.P;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, svd_cluster_kernel<S, R>, Cm, lam_l, chi, q, p, Bnext, lam_next, rep,
+                       plan.global ? A : (cplx<S>*)nullptr, (unsigned)plan.smem);
+    return;
+  }
+  const size_t full = svd_smem_bytes<S>(mcap, ncap, true);
+  const bool use_smem = full + 2048 <= max_dyn_smem();
+  const size_t smem = svd_smem_bytes<S>(mcap, ncap, use_smem);
+  svd_set_attr<S, R>();
+  const int warps = std::min(32, std::max(1, ncap / 2));
+  svd_truncate_kernel<S, R><<<1, 32 * warps, smem, s>>>(A, V, use_smem ? 1 : 0, chi, q, p, Bnext, lam_next, rep);
 }
 
 template <typename R, typename S>
@@ -275,7 +317,12 @@ static void launch_two_qubit(mps_state* st, const DevGate* g, int q, cudaStream_
   const dim3 g1((cap_r + kTile - 1) / kTile, (cap_l + kTile - 1) / kTile);
   const SvdPlan plan = cluster_svd_plan<S, R>(2 * cap_l, 2 * cap_r);
   const int P = plan.P;
-  {
+  // split-product tensor-core contractions (complex64 states): the cluster
+  // SVD reads C itself, so they serve the bonds where it runs
+  const bool tcg = sizeof(R) == 4 && P && tc_gates_used(st, q);
+  if (tcg) {
+    tc_theta(st, g, q, s);
+  } else {
     KernelScope k(st->ctx, MPS_K_THETA);
     theta_kernel<R, S><<<g1, blk, 0, s>>>(site_ptr<R>(st, q), site_ptr<R>(st, q + 1), g,
                                           st->d_lam + st->lam_off[q], st->d_chi, q,
@@ -289,46 +336,13 @@ static void launch_two_qubit(mps_state* st, const DevGate* g, int q, cudaStream_
   p.tol = st->cfg.svd_tol;
   p.mixed = st->cfg.svd_fp64 == 2 ? 0 : 1;
   const dim3 g3((cap_m + kTile - 1) / kTile, (2 * cap_l + kTile - 1) / kTile);
-  if (P) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(P);
-    cfg.blockDim = dim3(plan.threads);  // one warp per column pair
-    cfg.dynamicSmemBytes = plan.smem;
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = P;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    {
-      KernelScope k(st->ctx, MPS_K_SVD);
-      cudaLaunchKernelEx(&cfg, svd_cluster_kernel<S, R>, (const cplx<R>*)reinterpret_cast<cplx<R>*>(st->d_C),
-                         (const double*)(st->d_lam + st->lam_off[q]), st->d_chi, q, p, site_ptr<R>(st, q + 1),
-                         st->d_lam + st->lam_off[q + 1], st->d_rep,
-                         plan.global ? reinterpret_cast<cplx<S>*>(st->d_A) : (cplx<S>*)nullptr, (unsigned)plan.smem);
-    }
-    {
-      KernelScope k(st->ctx, MPS_K_G3);
-      g3_kernel<R><<<g3, blk, 0, s>>>(reinterpret_cast<cplx<R>*>(st->d_C), site_ptr<R>(st, q + 1), st->d_chi, q,
-                                      st->d_rep, site_ptr<R>(st, q));
-    }
-    return;
-  }
-  const int mcap = 2 * cap_l, ncap = 2 * cap_r;
-  const size_t full = svd_smem_bytes<S>(mcap, ncap, true);
-  const bool use_smem = full + 2048 <= max_dyn_smem();
-  const size_t smem = svd_smem_bytes<S>(mcap, ncap, use_smem);
-  svd_set_attr<S, R>();
-  int warps = std::min(32, std::max(1, ncap / 2));
-  {
-    KernelScope k(st->ctx, MPS_K_SVD);
-    svd_truncate_kernel<S, R><<<1, 32 * warps, smem, s>>>(
-        reinterpret_cast<cplx<S>*>(st->d_A), reinterpret_cast<cplx<S>*>(st->d_V), use_smem ? 1 : 0, st->d_chi, q,
-        p, site_ptr<R>(st, q + 1), st->d_lam + st->lam_off[q + 1], st->d_rep);
-  }
-  {
+  const cplx<R>* Cm = reinterpret_cast<const cplx<R>*>(st->d_C);
+  launch_svd<R, S>(st->ctx, plan, 2 * cap_l, 2 * cap_r, p, Cm, reinterpret_cast<cplx<S>*>(st->d_A),
+                   reinterpret_cast<cplx<S>*>(st->d_V), st->d_lam + st->lam_off[q], st->d_chi, q,
+                   site_ptr<R>(st, q + 1), st->d_lam + st->lam_off[q + 1], st->d_rep, s);
+  if (tcg) {
+    tc_g3(st, q, s);
+  } else {
     KernelScope k(st->ctx, MPS_K_G3);
     g3_kernel<R><<<g3, blk, 0, s>>>(reinterpret_cast<cplx<R>*>(st->d_C), site_ptr<R>(st, q + 1), st->d_chi, q,
                                     st->d_rep, site_ptr<R>(st, q));
@@ -518,6 +532,7 @@ static void destroy_state(mps_state* st) {
     graph_destroy(c, st->graph);
     st->graph = nullptr;
   }
+  tc_gates_free(st);
   for (void* p : {st->d_B, (void*)st->d_lam, (void*)st->d_chi, (void*)st->d_site_off, (void*)st->d_lam_off,
                   (void*)st->d_bits, (void*)st->d_rep, st->d_C, st->d_A, st->d_V, (void*)st->d_gates,
                   (void*)st->d_bound, (void*)st->d_theta, st->d_L[0], st->d_L[1], st->d_M, (void*)st->d_vals,
@@ -532,6 +547,110 @@ static void host_gate_to_dev(const mps_gate& g, DevGate& d) {
   d.arity = g.arity;
   const int cnt = g.arity == 1 ? 4 : 16;
   for (int e = 0; e < cnt; ++e) d.u[e] = make_double2(g.u[2 * e], g.u[2 * e + 1]);
+}
+
+// ---- workspace and kernels of mps_truncated_svd (one theta on its own)
+struct SvdWork {
+  int mcap = 0, ncap = 0, sbytes = 0;
+  int* d_chi = nullptr;
+  DevReport* d_rep = nullptr;
+  double* d_ones = nullptr;
+  double* d_lam = nullptr;
+  void* d_A = nullptr;
+  void* d_V = nullptr;
+};
+
+void svd_work_free(mps_ctx* ctx) {
+  SvdWork* w = ctx->svdw;
+  if (!w) return;
+  for (void* p : {(void*)w->d_chi, (void*)w->d_rep, (void*)w->d_ones, (void*)w->d_lam, w->d_A, w->d_V})
+    dev_free(ctx, p);
+  delete w;
+  ctx->svdw = nullptr;
+}
+
+static __global__ void svd_setup_kernel(int* chi, int chi_l, int chi_r, DevReport* rep) {
+  if (threadIdx.x != 0) return;
+  chi[0] = chi_l;
+  chi[1] = 0;
+  chi[2] = chi_r;
+  rep->discarded_weight = 0.0;
+  rep->min_kept_sv = 1.0;
+  rep->inv_norm = 1.0;
+  rep->max_chi = 1;
+  rep->degenerate_cuts = 0;
+  rep->not_converged = 0;
+  rep->tc_error = 0;
+  rep->max_sweeps = 0;
+  rep->two_qubit_gates = 0;
+  rep->svd_flops = 0.0;
+  rep->sweeps_fp32 = rep->sweeps_fp64 = 0;
+  for (int i = 0; i < 4; ++i) rep->phase_cycles[i] = 0.0;
+}
+
+// column-major copy of the row-major theta (the single-CTA kernel's input; lam = 1)
+template <typename R, typename S>
+static __global__ void svd_c_to_a_kernel(const cplx<R>* __restrict__ C, int m, int n, cplx<S>* __restrict__ A) {
+  const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (t >= (size_t)m * n) return;
+  const int col = (int)(t / m), row = (int)(t % m);
+  A[t] = ccast<cplx<S>>(C[(size_t)row * n + col]);
+}
+
+// the kept singular values without the renormalisation of the gate update
+static __global__ void svd_finish_kernel(const int* chi, const DevReport* rep, const double* lam, double* s_out) {
+  const int k = chi[1];
+  const double nrm = 1.0 / rep->inv_norm;
+  for (int a = threadIdx.x; a < k; a += blockDim.x) s_out[a] = lam[a] * nrm;
+}
+
+template <typename R, typename S>
+static mps_status truncated_svd(mps_ctx* ctx, int m, int n, const void* C, const SvdParams& p, double* s_out,
+                                void* Vh_out) {
+  cudaStream_t s = ctx->stream;
+  SvdWork* w = ctx->svdw;
+  if (w && (m > w->mcap || n > w->ncap || (int)sizeof(S) > w->sbytes)) {
+    MPSV_CUDA(cudaStreamSynchronize(s));
+    svd_work_free(ctx);
+    w = nullptr;
+  }
+  if (!w) {
+    w = new SvdWork();
+    ctx->svdw = w;
+    w->mcap = m;
+    w->ncap = n;
+    w->sbytes = (int)sizeof(S);
+    const size_t celem = sizeof(cplx<S>);
+    mps_status rc = dev_alloc(ctx, (void**)&w->d_chi, 4 * sizeof(int));
+    if (rc == MPS_OK) rc = dev_alloc(ctx, (void**)&w->d_rep, sizeof(DevReport));
+    if (rc == MPS_OK) rc = dev_alloc(ctx, (void**)&w->d_ones, (size_t)m * sizeof(double));
+    if (rc == MPS_OK) rc = dev_alloc(ctx, (void**)&w->d_lam, (size_t)n * sizeof(double));
+    if (rc == MPS_OK)
+      rc = dev_alloc(ctx, &w->d_A, std::max((size_t)m * n, cluster_svd_workspace(m, n, sizeof(S))) * celem);
+    if (rc == MPS_OK) rc = dev_alloc(ctx, &w->d_V, (size_t)n * n * celem);
+    if (rc == MPS_OK) {
+      std::vector<double> ones(m, 1.0);
+      cudaError_t e = cudaMemcpyAsync(w->d_ones, ones.data(), m * sizeof(double), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) rc = cuda_fail(e, "mps_truncated_svd set-up");
+    }
+    if (rc != MPS_OK) {
+      svd_work_free(ctx);
+      return rc;
+    }
+  }
+  const SvdPlan plan = cluster_svd_plan<S, R>(m, n);
+  const cplx<R>* Cm = static_cast<const cplx<R>*>(C);
+  svd_setup_kernel<<<1, 32, 0, s>>>(w->d_chi, m / 2, n / 2, w->d_rep);
+  if (!plan.P) {
+    const size_t tot = (size_t)m * n;
+    svd_c_to_a_kernel<R, S><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Cm, m, n, static_cast<cplx<S>*>(w->d_A));
+  }
+  launch_svd<R, S>(ctx, plan, m, n, p, Cm, static_cast<cplx<S>*>(w->d_A), static_cast<cplx<S>*>(w->d_V), w->d_ones,
+                   w->d_chi, 0, static_cast<cplx<R>*>(Vh_out), w->d_lam, w->d_rep, s);
+  svd_finish_kernel<<<1, 256, 0, s>>>(w->d_chi, w->d_rep, w->d_lam, s_out);
+  MPSV_CUDA(cudaGetLastError());
+  return MPS_OK;
 }
 
 }  // namespace mpsv
@@ -646,6 +765,8 @@ void mps_ctx_destroy(mps_ctx* ctx) {
   DeviceGuard guard(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   collect_profile(ctx);
+  contract_work_free(ctx);
+  svd_work_free(ctx);
   for (cudaEvent_t e : ctx->pool) cudaEventDestroy(e);
   for (auto& kv : ctx->allocs) cudaFree(kv.first);
   ctx->allocs.clear();
@@ -668,7 +789,7 @@ mps_status mps_create(mps_ctx* ctx, int32_t n_qubits, const uint8_t* init_bits, 
     set_error("mps_create: chi_max = %d outside [1, 1024]", cfg->chi_max);
     return MPS_EINVAL;
   }
-  if (cfg->precision != MPS_PREC_FP64 && cfg->precision != MPS_PREC_FP32) {
+  if (cfg->precision < MPS_PREC_FP64 || cfg->precision > MPS_PREC_AUTO) {
     set_error("mps_create: unknown precision %d", cfg->precision);
     return MPS_EINVAL;
   }
@@ -685,9 +806,13 @@ mps_status mps_create(mps_ctx* ctx, int32_t n_qubits, const uint8_t* init_bits, 
   st->ctx = ctx;
   st->n = n_qubits;
   st->cfg = *cfg;
-  st->fp32 = cfg->precision == MPS_PREC_FP32;
+  st->fp32 = cfg->precision != MPS_PREC_FP64;
+  st->tc_gates = (cfg->precision == MPS_PREC_BF16X3 || cfg->precision == MPS_PREC_TF32X3 ||
+                  cfg->precision == MPS_PREC_AUTO)
+                     ? cfg->precision
+                     : 0;
   st->svd64 = cfg->svd_fp64 != 0;
-  st->tc = st->fp32 && cfg->tensor_cores != 0;
+  st->tc = st->fp32 && (cfg->tensor_cores != 0 || st->tc_gates != 0);
   const int n = n_qubits;
   st->cap.resize(n + 1);
   for (int b = 0; b <= n; ++b) st->cap[b] = bond_cap(b, n, cfg->chi_max);
@@ -727,6 +852,7 @@ mps_status mps_create(mps_ctx* ctx, int32_t n_qubits, const uint8_t* init_bits, 
   A(&st->d_C, max_mn * celem);
   A(&st->d_A, std::max(max_mn, max_stack) * selem);  // theta copy, or the cluster SVD's stacked columns
   A(&st->d_V, max_nn * selem);
+  if (rc == MPS_OK && st->tc_gates) rc = tc_gates_setup(st);
   if (rc != MPS_OK) {
     destroy_state(st);
     return rc;
@@ -973,6 +1099,66 @@ void mps_circuit_destroy(mps_circuit* c) {
   cudaStreamSynchronize(c->ctx->stream);
   dev_free(c->ctx, c->d_tmpl);
   delete c;
+}
+
+mps_status mps_truncated_svd(mps_ctx* ctx, int32_t precision, int32_t m, int32_t n, const void* C, int32_t chi_max,
+                             double trunc_rel, int32_t svd_fp64, double* s_out, void* Vh_out, int32_t* k_out,
+                             mps_report* report) {
+  if (!ctx || !C || !s_out || !Vh_out || !k_out) {
+    set_error("mps_truncated_svd: NULL argument");
+    return MPS_EINVAL;
+  }
+  if (precision != MPS_PREC_FP64 && precision != MPS_PREC_FP32) {
+    set_error("mps_truncated_svd: precision %d is not MPS_PREC_FP64 or MPS_PREC_FP32", precision);
+    return MPS_EINVAL;
+  }
+  if (m < 2 || n < 2 || m > 4096 || n > 4096 || (m & 1) || (n & 1)) {
+    set_error("mps_truncated_svd: %d x %d theta: both sizes must be even and in 2..4096", m, n);
+    return MPS_EINVAL;
+  }
+  if (chi_max < 1 || !(trunc_rel >= 0.0 && trunc_rel < 1.0) || svd_fp64 < 0 || svd_fp64 > 2) {
+    set_error("mps_truncated_svd: chi_max = %d, trunc_rel = %g, svd_fp64 = %d", chi_max, trunc_rel, svd_fp64);
+    return MPS_EINVAL;
+  }
+  DeviceGuard guard(ctx->device);
+  SvdParams p;
+  p.chi_max = chi_max;
+  p.max_sweeps = 60;
+  p.trunc_rel = trunc_rel;
+  p.tol = 0.0;
+  p.mixed = svd_fp64 == 2 ? 0 : 1;
+  mps_status rc;
+  if (precision == MPS_PREC_FP64)
+    rc = svd_fp64 ? truncated_svd<double, double>(ctx, m, n, C, p, s_out, Vh_out)
+                  : truncated_svd<double, float>(ctx, m, n, C, p, s_out, Vh_out);
+  else
+    rc = svd_fp64 ? truncated_svd<float, double>(ctx, m, n, C, p, s_out, Vh_out)
+                  : truncated_svd<float, float>(ctx, m, n, C, p, s_out, Vh_out);
+  if (rc != MPS_OK) return rc;
+  DevReport r;
+  int k = 0;
+  MPSV_CUDA(cudaMemcpyAsync(&r, ctx->svdw->d_rep, sizeof(r), cudaMemcpyDeviceToHost, ctx->stream));
+  MPSV_CUDA(cudaMemcpyAsync(&k, ctx->svdw->d_chi + 1, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  MPSV_CUDA(cudaStreamSynchronize(ctx->stream));
+  *k_out = k;
+  if (report) {
+    report->discarded_weight = r.discarded_weight;
+    report->min_kept_sv = r.min_kept_sv;
+    report->max_chi = r.max_chi;
+    report->degenerate_cuts = r.degenerate_cuts;
+    report->svd_not_converged = r.not_converged;
+    report->max_sweeps_used = r.max_sweeps;
+    report->two_qubit_gates = r.two_qubit_gates;
+    report->svd_flops = r.svd_flops;
+    report->svd_sweeps_fp32 = r.sweeps_fp32;
+    report->svd_sweeps_fp64 = r.sweeps_fp64;
+    for (int i = 0; i < 4; ++i) report->svd_phase_cycles[i] = r.phase_cycles[i];
+  }
+  if (r.not_converged) {
+    set_error("mps_truncated_svd: the Jacobi SVD reached its sweep cap; the result is used as it stands");
+    return MPS_ENOTCONV;
+  }
+  return MPS_OK;
 }
 
 mps_status mps_apply_circuit_async(mps_state* st, const mps_circuit* c, const double* theta, int theta_on_device) {

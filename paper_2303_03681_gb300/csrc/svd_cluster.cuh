@@ -36,7 +36,10 @@
 
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace mpsv {
 
@@ -129,6 +132,103 @@ __device__ __forceinline__ int jacobi_pair_reg(cplx<S> (&x)[kClusterRegs], cplx<
 
 
 
+// Double-float forms of the two pair steps (FP64-accurate sweeps; the columns
+// hold float4 = (re_h, re_l, im_h, im_l)).  The Gram entries accumulate in
+// double-float per lane and across the warp; the rotation (an FP32 angle
+// brought to unit norm in FP64, jacobi_rotation<double>) is applied in
+// double-float.
+__device__ __forceinline__ void ff_warp_sum4(ff& a, ff& b, ff& c, ff& d) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a = ff_add(a, ff_shfl_xor(a, o));
+    b = ff_add(b, ff_shfl_xor(b, o));
+    c = ff_add(c, ff_shfl_xor(c, o));
+    d = ff_add(d, ff_shfl_xor(d, o));
+  }
+}
+
+__device__ __forceinline__ void ff_gram_row(const float4& x, const float4& y, ff& alpha, ff& beta, ff& gr, ff& gi) {
+  const ff xr = re_of(x), xi = im_of(x), yr = re_of(y), yi = im_of(y);
+  alpha = ff_fma(xr, xr, ff_fma(xi, xi, alpha));
+  beta = ff_fma(yr, yr, ff_fma(yi, yi, beta));
+  gr = ff_fma(xr, yr, ff_fma(xi, yi, gr));
+  gi = ff_add(gi, ff_sub(ff_mul(xr, yi), ff_mul(xi, yr)));
+}
+
+// x' = c x - conj(s) y, y' = c y + s x with s = sr + i si
+__device__ __forceinline__ void ff_rotate(float4& x, float4& y, ff c, ff sr, ff si) {
+  const ff xr = re_of(x), xi = im_of(x), yr = re_of(y), yi = im_of(y);
+  const ff nxr = ff_sub(ff_mul(c, xr), ff_add(ff_mul(sr, yr), ff_mul(si, yi)));
+  const ff nxi = ff_sub(ff_mul(c, xi), ff_sub(ff_mul(sr, yi), ff_mul(si, yr)));
+  const ff nyr = ff_add(ff_mul(c, yr), ff_sub(ff_mul(sr, xr), ff_mul(si, xi)));
+  const ff nyi = ff_add(ff_mul(c, yi), ff_add(ff_mul(sr, xi), ff_mul(si, xr)));
+  x = cff(nxr, nxi);
+  y = cff(nyr, nyi);
+}
+
+__device__ __forceinline__ bool ff_angle(ff alpha, ff beta, ff gr, ff gi, double tol, double floor, double tiny, ff& c,
+                                         ff& sr, ff& si) {
+  double cd;
+  cplx<double> sph;
+  if (!jacobi_rotation<double>(ff_to_double(alpha), ff_to_double(beta), ff_to_double(gr), ff_to_double(gi), tol,
+                               floor, tiny, cd, sph))
+    return false;
+  c = ff_from_double(cd);
+  sr = ff_from_double(sph.x);
+  si = ff_from_double(sph.y);
+  return true;
+}
+
+__device__ __forceinline__ int ff_pair_smem(float4* ai, float4* aj, int m, int len, int lane, double tol, double floor,
+                                            double tiny) {
+  ff alpha = ff_make(0.f, 0.f), beta = alpha, gr = alpha, gi = alpha;
+  for (int r = lane; r < m; r += 32) ff_gram_row(ai[r], aj[r], alpha, beta, gr, gi);
+  ff_warp_sum4(alpha, beta, gr, gi);
+  ff c, sr, si;
+  if (!ff_angle(alpha, beta, gr, gi, tol, floor, tiny, c, sr, si)) return 0;
+  for (int r = lane; r < len; r += 32) {
+    float4 x = ai[r], y = aj[r];
+    ff_rotate(x, y, c, sr, si);
+    ai[r] = x;
+    aj[r] = y;
+  }
+  return 1;
+}
+
+__device__ __forceinline__ int ff_pair_reg(float4 (&x)[kClusterRegs], float4* aj, int m, int len, int lane,
+                                           double tol, double floor, double tiny) {
+  ff alpha = ff_make(0.f, 0.f), beta = alpha, gr = alpha, gi = alpha;
+#pragma unroll
+  for (int i = 0; i < kClusterRegs; ++i) {
+    const int r = lane + 32 * i;
+    if (r < m) ff_gram_row(x[i], aj[r], alpha, beta, gr, gi);
+  }
+  ff_warp_sum4(alpha, beta, gr, gi);
+  ff c, sr, si;
+  if (!ff_angle(alpha, beta, gr, gi, tol, floor, tiny, c, sr, si)) return 0;
+#pragma unroll
+  for (int i = 0; i < kClusterRegs; ++i) {
+    const int r = lane + 32 * i;
+    if (r < len) {
+      float4 y = aj[r];
+      ff_rotate(x[i], y, c, sr, si);
+      aj[r] = y;
+    }
+  }
+  return 1;
+}
+
+// |z|^2 of a stored column entry in double (complex S or double-float)
+template <bool kDF, typename C>
+__device__ __forceinline__ double entry_nrm2(const C* col, int r) {
+  if constexpr (kDF) {
+    const double2 z = cff_to_double2(reinterpret_cast<const float4*>(col)[r]);
+    return z.x * z.x + z.y * z.y;
+  } else {
+    return double(col[r].x) * col[r].x + double(col[r].y) * col[r].y;
+  }
+}
+
 // Symmetric first-order orthonormalisation of the V parts (rows m .. len) of
 // two stacked columns: with e = v_i^H v_j, v_i -= conj(e)/2 v_j and
 // v_j -= e/2 v_i (from the old values).
@@ -200,17 +300,23 @@ struct ColStore {
 // norms of all columns (nrm2, through distributed shared memory) and marks
 // the columns the truncation discards (truncation_tail, into tail[]); a pair
 // of two marked columns is not rotated.
-template <typename T, int kOp, bool kGlobal>
+//
+// kDF: the columns hold double-float values (float4, see dfloat.cuh) and the
+// rotations run in double-float; T is double then.
+template <typename T, int kOp, bool kGlobal, bool kDF = false>
 __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColStore<T, kGlobal>& cs, int& cur, int max_sweeps, T tol, T floor,
                               T tiny, double trunc_rel, int chi_max, double* nrm2, int* tail, bool& converged,
                               const cg::cluster_group& cluster, int* s_flag_in, int* s_any) {
   using C = cplx<T>;
+  using E = std::conditional_t<kDF, float4, C>;  // a stored entry
+  static_assert(!kDF || (sizeof(float4) == sizeof(C) && kOp == 0), "double-float columns replace complex128 ones");
   // In the cross rounds, when every warp has one top-slot column, warp w
   // keeps it in registers for the b rotations it takes part in; only the
   // bottom-slot columns are re-read, so one barrier per sub-round orders
   // their hand-off.
   const bool cache_x = kOp == 0 && g.len <= 32 * kClusterRegs && g.b <= g.nw;
-  const T loose = T(2.0 / g.ncols);  // the tail rule's loose tolerance (pair_tol)
+  __shared__ double s_loose;
+  T loose = T(0);  // the tail rule's loose tolerance of the sweep (pair_tol)
   const bool active = g.member && g.wp < g.b;
   int sweep = 0;
   converged = false;
@@ -222,7 +328,7 @@ __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColSto
       for (int c = g.wp; g.member && c < 2 * g.b; c += g.nw) {
         const C* a = cs.col(cur, c / g.b, c % g.b, 0);
         double acc = 0.0;
-        for (int r = g.wl; r < g.m; r += 32) acc += double(a[r].x) * a[r].x + double(a[r].y) * a[r].y;
+        for (int r = g.wl; r < g.m; r += 32) acc += entry_nrm2<kDF>(a, r);
         acc = warp_sum(acc);
         if (g.wl == 0) {
           const int id = col_id(g, c / g.b, c % g.b, 0);
@@ -230,7 +336,10 @@ __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColSto
         }
       }
       cluster.sync();
-      if (g.member) truncation_tail(nrm2, g.ncols_pad, trunc_rel, chi_max, tail);
+      if (g.member) {
+        truncation_tail(nrm2, g.ncols_pad, trunc_rel, chi_max, tail, &s_loose);
+        loose = T(s_loose);
+      }
     }
     for (int rnd = 0; rnd < 2 * g.P - 1; ++rnd) {
       if (!g.member) {
@@ -253,20 +362,29 @@ __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColSto
             if (kOp == 0) {
               const T tl = pair_tol(tail[col_id(g, a0 / g.b, a0 % g.b, rnd)], tail[col_id(g, a1 / g.b, a1 % g.b, rnd)],
                                     tol, loose);
-              if (tl >= T(0)) rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tl, floor, tiny);
+              if (tl >= T(0)) {
+                if constexpr (kDF)
+                  rotated |= ff_pair_smem(reinterpret_cast<float4*>(x), reinterpret_cast<float4*>(y), g.m, g.len,
+                                          g.wl, tl, floor, tiny);
+                else
+                  rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tl, floor, tiny);
+              }
             } else
               orth_pair<T>(x, y, g.m, g.len, g.wl);
           }
           __syncthreads();
         }
       } else {
-        C xr[kClusterRegs];
-        C* xcol = cs.col(cur, 0, active ? g.wp : 0, rnd);
+        E xr[kClusterRegs];
+        E* xcol = reinterpret_cast<E*>(cs.col(cur, 0, active ? g.wp : 0, rnd));
         if (active && cache_x) {
 #pragma unroll
           for (int i = 0; i < kClusterRegs; ++i) {
             const int r = g.wl + 32 * i;
-            xr[i] = r < g.len ? xcol[r] : cmk<T>(0, 0);
+            if constexpr (kDF)
+              xr[i] = r < g.len ? xcol[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+            else
+              xr[i] = r < g.len ? xcol[r] : cmk<T>(0, 0);
           }
         }
         for (int sr = 0; sr < g.b; ++sr) {
@@ -274,9 +392,14 @@ __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColSto
             if (active) {
               const T tl = pair_tol(tail[col_id(g, 0, g.wp, rnd)], tail[col_id(g, 1, (g.wp + sr) % g.b, rnd)], tol,
                                     loose);
-              if (tl >= T(0))
-                rotated |= jacobi_pair_reg<T>(xr, cs.col(cur, 1, (g.wp + sr) % g.b, rnd), g.m, g.len, g.wl, tl,
-                                              floor, tiny);
+              if (tl >= T(0)) {
+                if constexpr (kDF)
+                  rotated |= ff_pair_reg(xr, reinterpret_cast<float4*>(cs.col(cur, 1, (g.wp + sr) % g.b, rnd)), g.m,
+                                         g.len, g.wl, tl, floor, tiny);
+                else
+                  rotated |= jacobi_pair_reg<T>(xr, cs.col(cur, 1, (g.wp + sr) % g.b, rnd), g.m, g.len, g.wl, tl,
+                                                floor, tiny);
+              }
             }
           } else {
             for (int pw = g.wp; pw < g.b; pw += g.nw) {
@@ -285,7 +408,13 @@ __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColSto
               if (kOp == 0) {
                 const T tl = pair_tol(tail[col_id(g, 0, pw, rnd)], tail[col_id(g, 1, (pw + sr) % g.b, rnd)], tol,
                                       loose);
-                if (tl >= T(0)) rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tl, floor, tiny);
+                if (tl >= T(0)) {
+                  if constexpr (kDF)
+                    rotated |= ff_pair_smem(reinterpret_cast<float4*>(x), reinterpret_cast<float4*>(y), g.m, g.len,
+                                            g.wl, tl, floor, tiny);
+                  else
+                    rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tl, floor, tiny);
+                }
               } else
                 orth_pair<T>(x, y, g.m, g.len, g.wl);
             }
@@ -375,7 +504,9 @@ __host__ __device__ inline size_t cluster_svd_workspace(size_t mcap, size_t ncap
 
 // Everything after the geometry: the column layout (shared or global) is a
 // compile-time choice so that shared-memory accesses compile as such.
-template <typename S, typename R, bool kGlobal>
+// kDF: the FP64-accurate sweeps of the mixed form run in double-float (the
+// rebuilt FP64 columns are converted in place; see dfloat.cuh).
+template <typename S, typename R, bool kGlobal, bool kDF>
 __device__ __forceinline__ void svd_cluster_body(const ClusterGeom& g, const cg::cluster_group& cluster,
                                                  const cplx<R>* __restrict__ Cm, const double* __restrict__ lam_l,
                                                  int* __restrict__ chi, int q, const SvdParams& p,
@@ -509,13 +640,25 @@ __device__ __forceinline__ void svd_cluster_body(const ClusterGeom& g, const cg:
       x[r] = cmk<S>(w * ar, w * ai);
     }
     __syncthreads();
+    if constexpr (kDF) {
+      // the stacked FP64 columns of this CTA to double-float, in place
+      for (size_t t = threadIdx.x; g.member && t < (size_t)2 * b * len; t += nt) {
+        C* col = cs.col(cur, (int)(t / ((size_t)b * len)), (int)((t / len) % b), 0);
+        const int r = (int)(t % len);
+        const double2 z = make_double2(double(col[r].x), double(col[r].y));
+        reinterpret_cast<float4*>(col)[r] = cff_from_double2(z);
+      }
+      __syncthreads();
+    }
     t_fix = clock64();
   }
-  const S eps_u = sizeof(S) == 8 ? S(1.1102230246251565e-16) : S(5.9604645e-08f);
+  // unit roundoff of the last sweeps: FP64, double-float (about 48 bits with
+  // the sloppy additions of dfloat.cuh: 2^-46 to be safe) or FP32
+  const S eps_u = kDF ? S(1.4210854715202004e-14) : (sizeof(S) == 8 ? S(1.1102230246251565e-16) : S(5.9604645e-08f));
   const S tol = p.tol > 0 ? S(p.tol) : S(tol_scale) * eps_u;
   const S floor = S(16.0 * double(eps_u) * double(eps_u) * fro2);
   const S tiny = sizeof(S) == 8 ? S(1e-290) : S(1e-35f);
-  used += cluster_sweeps<S, 0, kGlobal>(g, cs, cur, p.max_sweeps, tol, floor, tiny, p.trunc_rel, p.chi_max, nrm2, tail,
+  used += cluster_sweeps<S, 0, kGlobal, kDF>(g, cs, cur, p.max_sweeps, tol, floor, tiny, p.trunc_rel, p.chi_max, nrm2, tail,
                                         converged, cluster, s_flag_in, s_any);
   const int sweep = used;
 
@@ -525,7 +668,7 @@ __device__ __forceinline__ void svd_cluster_body(const ClusterGeom& g, const cg:
   for (int c = warp; g.member && c < 2 * b; c += g.nw) {
     const C* a = cs.col(cur, c / b, c % b, 0);
     double acc = 0.0;
-    for (int r = lane; r < m; r += 32) acc += double(a[r].x) * a[r].x + double(a[r].y) * a[r].y;
+    for (int r = lane; r < m; r += 32) acc += entry_nrm2<kDF>(a, r);
     acc = warp_sum(acc);
     if (lane == 0) {
       const double sv = sqrt(acc);
@@ -606,7 +749,13 @@ __device__ __forceinline__ void svd_cluster_body(const ClusterGeom& g, const cg:
     const int a = rnk[gc];
     if (a >= k) continue;
     const C* v = cs.col(cur, c / b, c % b, 0) + m;
-    for (int r = lane; r < ncols; r += 32) Bnext[(size_t)a * ncols + r] = ccast<cplx<R>>(cconj(v[r]));
+    for (int r = lane; r < ncols; r += 32) {
+      if constexpr (kDF)
+        Bnext[(size_t)a * ncols + r] =
+            ccast<cplx<R>>(cconj(cff_to_double2(reinterpret_cast<const float4*>(v)[r])));
+      else
+        Bnext[(size_t)a * ncols + r] = ccast<cplx<R>>(cconj(v[r]));
+    }
   }
   cluster.sync();  // no CTA leaves while its shared memory may still be read
 }
@@ -645,19 +794,48 @@ __global__ void __launch_bounds__(kClusterMaxThreads<S>, 1)
   // the cluster barriers in step.
   const int per = sizeof(S) == 8 ? 1 : g.nw;
   g.P = min(g.Pl, max(1, (g.ncols + 2 * per - 1) / (2 * per)));
+  // Without a global workspace the columns must fit the launch's shared
+  // memory: fewer CTAs mean wider blocks (an FP32 theta of 96 columns takes 3
+  // CTAs of 16 columns where the capacity plan sized 4 of 12), so spread them
+  // over more of the launched CTAs until they fit.  The plan guarantees that
+  // all Pl CTAs fit the capacity, hence the actual sizes.
+  while (gbuf == nullptr && g.P < g.Pl) {
+    const int bb = (g.ncols + 2 * g.P - 1) / (2 * g.P);
+    if (ClusterSvdSmem<S>(bb, g.len, 2 * g.P * bb, g.nt).total <= smem_bytes) break;
+    ++g.P;
+  }
   g.member = g.me < g.P;
   g.b = (g.ncols + 2 * g.P - 1) / (2 * g.P);  // a warp takes pairs w, w + nw, ...
   g.ncols_pad = 2 * g.P * g.b;
 
   // Shared memory when the stacked columns fit the launch's allocation, else the global workspace.
-  const bool in_smem =
-      gbuf == nullptr || ClusterSvdSmem<S>(g.b, g.len, g.ncols_pad, g.nt).total <= smem_bytes;
+  const bool fits = ClusterSvdSmem<S>(g.b, g.len, g.ncols_pad, g.nt).total <= smem_bytes;
+  if (!fits && gbuf == nullptr) {
+    // unreachable for launches sized by the host plan; leave without touching
+    // the state (every CTA returns before any cluster barrier) and report it
+    // as a sweep-cap hit so that the caller sees MPS_ENOTCONV
+    if (g.me == 0 && threadIdx.x == 0) atomicAdd(&rep->not_converged, 1);
+    return;
+  }
+  const bool in_smem = fits;
+  // the mixed form's FP64-accurate sweeps run in double-float
+  if constexpr (sizeof(S) == 8) {
+    if (p.mixed) {
+      if (in_smem)
+        svd_cluster_body<S, R, false, true>(g, cluster, Cm, lam_l, chi, q, p, Bnext, lam_next, rep, gbuf, smem,
+                                            s_flag_in, s_fro, s_k, s_nrm, &s_any, t_start);
+      else
+        svd_cluster_body<S, R, true, true>(g, cluster, Cm, lam_l, chi, q, p, Bnext, lam_next, rep, gbuf, smem,
+                                           s_flag_in, s_fro, s_k, s_nrm, &s_any, t_start);
+      return;
+    }
+  }
   if (in_smem)
-    svd_cluster_body<S, R, false>(g, cluster, Cm, lam_l, chi, q, p, Bnext, lam_next, rep, gbuf, smem, s_flag_in,
-                                  s_fro, s_k, s_nrm, &s_any, t_start);
+    svd_cluster_body<S, R, false, false>(g, cluster, Cm, lam_l, chi, q, p, Bnext, lam_next, rep, gbuf, smem, s_flag_in,
+                                         s_fro, s_k, s_nrm, &s_any, t_start);
   else
-    svd_cluster_body<S, R, true>(g, cluster, Cm, lam_l, chi, q, p, Bnext, lam_next, rep, gbuf, smem, s_flag_in,
-                                 s_fro, s_k, s_nrm, &s_any, t_start);
+    svd_cluster_body<S, R, true, false>(g, cluster, Cm, lam_l, chi, q, p, Bnext, lam_next, rep, gbuf, smem, s_flag_in,
+                                        s_fro, s_k, s_nrm, &s_any, t_start);
 }
 
 }  // namespace mpsv

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libmpsvqe.so")
 MPS_OK, MPS_EINVAL, MPS_ENOMEM, MPS_ECUDA, MPS_ETIMEOUT, MPS_ENOTCONV, MPS_EBUSY, MPS_ESTATE = range(8)
 STATUS_NAMES = ["MPS_OK", "MPS_EINVAL", "MPS_ENOMEM", "MPS_ECUDA", "MPS_ETIMEOUT", "MPS_ENOTCONV", "MPS_EBUSY",
                 "MPS_ESTATE"]
-PRECISIONS = {"fp64": 0, "fp32": 1}
+PRECISIONS = {"fp64": 0, "fp32": 1, "bf16x3": 2, "tf32x3": 3, "auto": 4}
 KERNEL_KINDS = ["theta", "svd", "g3", "gate1", "setup", "env_m", "env_child", "env_leaf", "env_trace", "reduce"]
 
 # numpy views of the C structs (layouts match include/mps_vqe.h on LP64 hosts)
@@ -104,6 +104,9 @@ def _load():
         "mps_server_destroy": ([P], None),
         "mps_ctx_profile": ([P, ctypes.c_uint32], ctypes.c_int),
         "mps_ctx_set_graphs": ([P, I32], ctypes.c_int),
+        "mps_contract_theta": ([P, I32, I32, I32, I32, P, P, P, P], ctypes.c_int),
+        "mps_truncated_svd": ([P, I32, I32, I32, P, I32, D, I32, P, P, ctypes.POINTER(I32), ctypes.POINTER(Report)],
+                              ctypes.c_int),
         "mps_ctx_profile_read": ([P, I32, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                   ctypes.POINTER(D), I32], ctypes.c_int),
     }
@@ -435,6 +438,33 @@ class State(_Child):
         rep = Report()
         _check(_lib.mps_get_report(self.handle, ctypes.byref(rep)))
         return rep.as_dict()
+
+
+def contract_theta(ctx: Context, precision: str, chi_l: int, chi_m: int, chi_r: int, b_left_ptr: int,
+                   b_right_ptr: int, gate, c_out_ptr: int):
+    """C = Q (B_q B_{q+1}) on complex64 device arrays (mps_contract_theta);
+    asynchronous on the context stream."""
+    g = np.ascontiguousarray(np.stack([np.real(gate), np.imag(gate)], axis=-1).reshape(-1), dtype=np.float64)
+    if g.shape != (32,):
+        raise ValueError("gate must be 4x4")
+    _check(_lib.mps_contract_theta(ctx.handle, PRECISIONS[precision], int(chi_l), int(chi_m), int(chi_r),
+                                   ctypes.c_void_p(int(b_left_ptr)), ctypes.c_void_p(int(b_right_ptr)), _ptr(g),
+                                   ctypes.c_void_p(int(c_out_ptr))))
+
+
+def truncated_svd(ctx: Context, precision: str, m: int, n: int, c_ptr: int, chi_max: int, trunc_rel: float,
+                  svd_fp64: int, s_out_ptr: int, vh_out_ptr: int):
+    """Truncated SVD of an m x n device theta (mps_truncated_svd).  Returns
+    (k, report, status); MPS_ENOTCONV is returned as the status, with the
+    results written, rather than raised."""
+    k = ctypes.c_int32()
+    rep = Report()
+    rc = _lib.mps_truncated_svd(ctx.handle, PRECISIONS[precision], int(m), int(n), ctypes.c_void_p(int(c_ptr)),
+                                int(chi_max), float(trunc_rel), int(svd_fp64), ctypes.c_void_p(int(s_out_ptr)),
+                                ctypes.c_void_p(int(vh_out_ptr)), ctypes.byref(k), ctypes.byref(rep))
+    if rc not in (MPS_OK, MPS_ENOTCONV):
+        _check(rc)
+    return k.value, rep.as_dict(), rc
 
 
 def vqe_eval(ctx: Context, requests):
