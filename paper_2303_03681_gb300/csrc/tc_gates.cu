@@ -38,6 +38,7 @@ struct ThetaSrcA {
 // 32 t + 31 for j = 0 (columns 0-31 of the tile) and j = 1 (32-63), so the
 // epilogue finds both j of one a_r in one CTA.
 struct ThetaSrcB {
+  static constexpr bool kAlongN = true;  // consecutive a_r of one (k, j) are consecutive in memory
   const float2* Bq1;
   const int* chi;
   int q;
@@ -54,7 +55,8 @@ struct ThetaSrcB {
 };
 
 // out[(a_l, i), (j, a_r)] = sum_{i', j'} Q[2i + j][2i' + j'] acc[(a_l, i')][(j', a_r)],
-// stored unscaled (the SVD kernel applies lam_q to its rows).
+// stored unscaled (the SVD kernel applies lam_q to its rows).  Output run h
+// of a row is j = h: the 32 a_r of the tile at columns h chi_r + a_r.
 struct ThetaEpi {
   const int* chi;
   int q;
@@ -65,10 +67,8 @@ struct ThetaEpi {
     kr = 2 * chi[q + 1];
     ncols = (chi[q + 2] + 31) / 32 * 64;
   }
-  __device__ void operator()(int row, int nbase, const float (&acc)[kBNr], int lane) const {
-    (void)lane;
-    const int chi_l = chi[q], chi_r = chi[q + 2];
-    const int n = 2 * chi_r;
+  __device__ void values(int row, int nbase, const float (&acc)[kBNr], float2 (&v)[64]) const {
+    (void)nbase;
     const int i = row & 1;
     float2 g[2][4];
 #pragma unroll
@@ -78,8 +78,6 @@ struct ThetaEpi {
         const double2 u = gate->u[(2 * i + j) * 4 + e];
         g[j][e] = make_float2(float(u.x), float(u.y));
       }
-    const int ar0 = (nbase / 64) * 32;
-    const bool row_ok = row < 2 * chi_l;
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
       const float2 own0 = make_float2(acc[2 * c], acc[2 * c + 1]);
@@ -89,8 +87,6 @@ struct ThetaEpi {
       oth0.y = __shfl_xor_sync(0xffffffffu, own0.y, 1);
       oth1.x = __shfl_xor_sync(0xffffffffu, own1.x, 1);
       oth1.y = __shfl_xor_sync(0xffffffffu, own1.y, 1);
-      const int ar = ar0 + c;
-      if (!row_ok || ar >= chi_r) continue;
       // value at (i', j'): i' == i -> own, else the partner's
       const float2 v00 = i == 0 ? own0 : oth0, v01 = i == 0 ? own1 : oth1;
       const float2 v10 = i == 1 ? own0 : oth0, v11 = i == 1 ? own1 : oth1;
@@ -101,9 +97,16 @@ struct ThetaEpi {
         cfma(o, g[j][1], v01);
         cfma(o, g[j][2], v10);
         cfma(o, g[j][3], v11);
-        Cm[(size_t)row * n + j * chi_r + ar] = o;
+        v[32 * j + c] = o;
       }
     }
+  }
+  __device__ float2* run(int row, int nbase, int h, int& count) const {
+    const int chi_r = chi[q + 2];
+    const int ar0 = (nbase / 64) * 32;
+    if (row >= 2 * chi[q] || ar0 >= chi_r) return nullptr;
+    count = min(32, chi_r - ar0);
+    return Cm + (size_t)row * (2 * chi_r) + h * chi_r + ar0;
   }
 };
 
@@ -120,6 +123,7 @@ struct G3SrcA {
 };
 
 struct G3SrcB {
+  static constexpr bool kAlongN = false;  // consecutive kk of one a are consecutive in memory
   const float2* Bn;
   const int* chi;
   int q;
@@ -145,16 +149,19 @@ struct G3Epi {
     kr = 4 * chi[q + 2];
     ncols = (chi[q + 1] + 63) / 64 * 64;
   }
-  __device__ void operator()(int row, int nbase, const float (&acc)[kBNr], int lane) const {
-    (void)lane;
-    const int k = chi[q + 1];
-    if (row >= 2 * chi[q]) return;
+  __device__ void values(int row, int nbase, const float (&acc)[kBNr], float2 (&v)[64]) const {
+    (void)row;
+    (void)nbase;
     const float inv = float(rep->inv_norm);
 #pragma unroll
-    for (int c = 0; c < kBNc; ++c) {
-      const int a = nbase + c;
-      if (a < k) Bout[(size_t)row * k + a] = make_float2(acc[2 * c] * inv, acc[2 * c + 1] * inv);
-    }
+    for (int c = 0; c < kBNc; ++c) v[c] = make_float2(acc[2 * c] * inv, acc[2 * c + 1] * inv);
+  }
+  // run h: new bond indices nbase + 32 h ..
+  __device__ float2* run(int row, int nbase, int h, int& count) const {
+    const int k = chi[q + 1], a0 = nbase + 32 * h;
+    if (row >= 2 * chi[q] || a0 >= k) return nullptr;
+    count = min(32, k - a0);
+    return Bout + (size_t)row * k + a0;
   }
 };
 
@@ -210,12 +217,16 @@ template <int M> void set_attrs() {
   });
 }
 
-// Blocks of 256 threads for `elems` work items (grid-stride beyond 152 x 32 blocks).
-unsigned split_grid(size_t elems) {
-  return (unsigned)std::max<size_t>(1, std::min<size_t>((elems + 255) / 256, 152 * 32));
+// The GEMM over a grid of (column tiles, row tiles).
+template <int M, class Epi>
+void launch_gemm(const TcWork& w, dim3 grid, const Epi& epi, int* err, cudaStream_t s) {
+  cgemm_tma_kernel<M, Epi><<<grid, kThreads, kSmemBytes, s>>>(w.maps[0], w.maps[1], w.maps[2], w.maps[3], epi, err);
 }
 
-// The three launches of the theta contraction for bond capacities (cap_l,
+// Blocks of 256 threads for `items` work items (grid-stride beyond 152 x 16 blocks).
+int split_blocks(size_t items) { return (int)std::max<size_t>(1, std::min<size_t>((items + 255) / 256, 152 * 16)); }
+
+// The two launches of the theta contraction for bond capacities (cap_l,
 // cap_m, cap_r) around sites (q, q+1); the actual dimensions are chi[q..q+2].
 template <int M>
 void launch_theta_raw(const TcWork& w, const float2* Bq, const float2* Bq1, const int* chi, int q, int cap_l,
@@ -223,12 +234,12 @@ void launch_theta_raw(const TcWork& w, const float2* Bq, const float2* Bq1, cons
   using T = typename ModeTraits<M>::T;
   T* p[4];
   for (int i = 0; i < 4; ++i) p[i] = static_cast<T*>(w.planes[i]);
-  const int npad_cap = (cap_r + 31) / 32 * 64;
-  split_ab_kernel<M><<<split_grid(((size_t)2 * cap_l + npad_cap) * (cap_m + 2) / 2), 256, 0, s>>>(
-      ThetaSrcA{Bq, chi, q}, ThetaSrcB{Bq1, chi, q}, w.ld, p[0], p[1], p[2], p[3]);
-  const dim3 grid(npad_cap / kBNc, (2 * cap_l + kBM - 1) / kBM);
-  cgemm_tma_kernel<M, ThetaEpi><<<grid, kThreads, kSmemBytes, s>>>(w.maps[0], w.maps[1], w.maps[2], w.maps[3],
-                                                                  ThetaEpi{chi, q, g, Cm}, err);
+  const int npad_cap = (cap_r + 31) / 32 * 64, kpad_cap = pad_k(2 * cap_m, M) / 2;
+  const int a_blocks = split_blocks((size_t)2 * cap_l * kpad_cap / 2);
+  const int b_tiles = ((npad_cap + kSplitTile - 1) / kSplitTile) * ((kpad_cap + kSplitTile - 1) / kSplitTile);
+  split_ab_kernel<M><<<a_blocks + std::min(b_tiles, 152 * 16), 256, 0, s>>>(
+      ThetaSrcA{Bq, chi, q}, ThetaSrcB{Bq1, chi, q}, w.ld, a_blocks, p[0], p[1], p[2], p[3]);
+  launch_gemm<M>(w, dim3(npad_cap / kBNc, (2 * cap_l + kBM - 1) / kBM), ThetaEpi{chi, q, g, Cm}, err, s);
 }
 
 template <int M>
@@ -250,14 +261,14 @@ void launch_g3(mps_state* st, int q, cudaStream_t s) {
   T* p[4];
   for (int i = 0; i < 4; ++i) p[i] = static_cast<T*>(w.planes[i]);
   KernelScope k(st->ctx, MPS_K_G3);
-  const int npad_cap = (cap_m + 63) / 64 * 64;
-  split_ab_kernel<M><<<split_grid(((size_t)2 * cap_l + npad_cap) * (cap_r + 1)), 256, 0, s>>>(
-      G3SrcA{reinterpret_cast<const float2*>(st->d_C), st->d_chi, q}, G3SrcB{Bn, st->d_chi, q}, w.ld, p[0], p[1],
-      p[2], p[3]);
-  const dim3 grid(npad_cap / kBNc, (2 * cap_l + kBM - 1) / kBM);
-  cgemm_tma_kernel<M, G3Epi><<<grid, kThreads, kSmemBytes, s>>>(w.maps[0], w.maps[1], w.maps[2], w.maps[3],
-                                                               G3Epi{st->d_chi, q, st->d_rep, Bout},
-                                                               &st->d_rep->tc_error);
+  const int npad_cap = (cap_m + 63) / 64 * 64, kpad_cap = pad_k(4 * cap_r, M) / 2;
+  const int a_blocks = split_blocks((size_t)2 * cap_l * kpad_cap / 2);
+  const int b_blocks = split_blocks((size_t)npad_cap * kpad_cap / 2);
+  split_ab_kernel<M><<<a_blocks + b_blocks, 256, 0, s>>>(
+      G3SrcA{reinterpret_cast<const float2*>(st->d_C), st->d_chi, q}, G3SrcB{Bn, st->d_chi, q}, w.ld, a_blocks, p[0],
+      p[1], p[2], p[3]);
+  launch_gemm<M>(w, dim3(npad_cap / kBNc, (2 * cap_l + kBM - 1) / kBM), G3Epi{st->d_chi, q, st->d_rep, Bout},
+                 &st->d_rep->tc_error, s);
 }
 
 }  // namespace

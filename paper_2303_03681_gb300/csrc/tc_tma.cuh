@@ -25,11 +25,12 @@
 // warps: warp 0 issues the TMA loads of a three-stage shared-memory ring
 // (per stage: 128 rows x 128 bytes of A_hi, A_lo, B_hi and B_lo, 128-byte
 // swizzled, 64 KB), warp 1 allocates tensor memory and issues the
-// tcgen05.mma of each 128-byte K chunk (12 TF32 or 6 BF16 instructions, 3
+// tcgen05.mma of each 128-byte K chunk (12 TF32 or 12 BF16 instructions, 3
 // products each) into one of two 128-column accumulators, and warps 2-5 drain
-// each finished chunk accumulator with tcgen05.ld into FP32 registers (the
-// tensor cores' own accumulation chain stays one chunk long) and, at the end,
-// apply the epilogue of the contraction.  mbarriers order every hand-over;
+// each finished accumulator (kDrain chunks: the tensor cores' own
+// accumulation chain stays that long) with tcgen05.ld into FP32 registers
+// and, at the end, apply the epilogue of the contraction, staging the rows
+// in shared memory so that the global stores coalesce.  mbarriers order every hand-over;
 // every wait is bounded (2 s): a wait that runs out raises a CTA-wide abort
 // flag, every role stops issuing, the error flag is set and tensor memory is
 // released.
@@ -58,7 +59,7 @@ constexpr uint64_t kWaitNs = 2000000000ull;
 // K chunks accumulated in one tensor-memory buffer before the epilogue warps
 // drain it into FP32 registers (the length of the tensor cores' own
 // accumulation chain, in chunks)
-constexpr int kDrain = 1;
+constexpr int kDrain = 4;
 
 enum Mode { kTF32 = 0, kBF16 = 1 };
 
@@ -228,28 +229,53 @@ template <> struct Quad<kBF16> {
   }
 };
 
-// Both operands of one GEMM in one launch; a thread handles two consecutive
-// complex K values (four real columns: 16- or 8-byte stores along a row).
-//  * A (SrcA: dims(rows, K), a(r, k)): row r, real columns 2k + t.
+// Both operands of one GEMM in one launch.  Blocks [0, a_blocks) write the
+// A planes, the others the B planes.
+//  * A (SrcA: dims(rows, K), a(r, k)): row r, real columns 2k + t; a thread
+//    handles two consecutive complex K values (four real columns: 16- or
+//    8-byte stores along a row), so reads and writes run along K.
 //  * B (SrcB: dims(N_pad, K), b(k, n, ok)): the 2 x 2 real embedding, row 2n =
 //    (Re b, -Im b) and row 2n + 1 = (Im b, Re b) along 2k + t; padding
-//    columns (ok cleared) give zero rows.
+//    columns (ok cleared) give zero rows.  Where consecutive n of one k are
+//    consecutive in memory (SrcB::kAlongN, the theta's right site tensor) a
+//    block stages a 32 k x 32 n tile in shared memory, read along n and
+//    written along K; otherwise threads run along K as for A.
 // Real columns from 2K up to the chunk boundary are written as zeros; sizes
 // come from device memory, so the grid is sized for the capacities.
+template <int M>
+__device__ __forceinline__ void store_b_pair(typename ModeTraits<M>::T* bhi, typename ModeTraits<M>::T* blo, int ld,
+                                             int n, int k, float2 v0, float2 v1) {
+  using T = typename ModeTraits<M>::T;
+  T hr0, lr0, hi0, li0, hn0, ln0, hr1, lr1, hi1, li1, hn1, ln1;
+  Split<M>::run(v0.x, hr0, lr0);
+  Split<M>::run(v0.y, hi0, li0);
+  Split<M>::run(-v0.y, hn0, ln0);
+  Split<M>::run(v1.x, hr1, lr1);
+  Split<M>::run(v1.y, hi1, li1);
+  Split<M>::run(-v1.y, hn1, ln1);
+  const size_t o0 = (size_t)(2 * n) * ld + 2 * k, o1 = o0 + ld;
+  Quad<M>::store(bhi + o0, hr0, hn0, hr1, hn1);
+  Quad<M>::store(bhi + o1, hi0, hr0, hi1, hr1);
+  Quad<M>::store(blo + o0, lr0, ln0, lr1, ln1);
+  Quad<M>::store(blo + o1, li0, lr0, li1, lr1);
+}
+
+constexpr int kSplitTile = 32;  // k and n extent of a staged B tile
+
 template <int M, class SrcA, class SrcB>
-__global__ void __launch_bounds__(256) split_ab_kernel(SrcA sa, SrcB sb, int ld, typename ModeTraits<M>::T* __restrict__ ahi,
+__global__ void __launch_bounds__(256) split_ab_kernel(SrcA sa, SrcB sb, int ld, int a_blocks,
+                                                        typename ModeTraits<M>::T* __restrict__ ahi,
                                                         typename ModeTraits<M>::T* __restrict__ alo,
                                                         typename ModeTraits<M>::T* __restrict__ bhi,
                                                         typename ModeTraits<M>::T* __restrict__ blo) {
   using T = typename ModeTraits<M>::T;
-  int rows, Ka, npad, Kb;
-  sa.dims(rows, Ka);
-  sb.dims(npad, Kb);
-  const int pa = pad_k(2 * Ka, M) / 4, pb = pad_k(2 * Kb, M) / 4;  // k pairs per row
-  const long long na = (long long)rows * pa, total = na + (long long)npad * pb;
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-       e += (long long)gridDim.x * blockDim.x) {
-    if (e < na) {
+  __shared__ float2 tile[kSplitTile][kSplitTile + 1];
+  if ((int)blockIdx.x < a_blocks) {
+    int rows, Ka;
+    sa.dims(rows, Ka);
+    const int pa = pad_k(2 * Ka, M) / 4;  // k pairs per row
+    const long long na = (long long)rows * pa;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < na; e += (long long)a_blocks * blockDim.x) {
       const int r = (int)(e / pa), k = 2 * (int)(e % pa);
       const float2 v0 = k < Ka ? sa(r, k) : make_float2(0.f, 0.f);
       const float2 v1 = k + 1 < Ka ? sa(r, k + 1) : make_float2(0.f, 0.f);
@@ -261,27 +287,47 @@ __global__ void __launch_bounds__(256) split_ab_kernel(SrcA sa, SrcB sb, int ld,
       const size_t o = (size_t)r * ld + 2 * k;
       Quad<M>::store(ahi + o, h[0], h[1], h[2], h[3]);
       Quad<M>::store(alo + o, l[0], l[1], l[2], l[3]);
-    } else {
-      const long long eb = e - na;
-      const int n = (int)(eb / pb), k = 2 * (int)(eb % pb);
+    }
+    return;
+  }
+  int npad, Kb;
+  sb.dims(npad, Kb);
+  const int pb = pad_k(2 * Kb, M) / 4;  // k pairs per embedded row
+  const int bblk = (int)blockIdx.x - a_blocks, nbblk = (int)gridDim.x - a_blocks;
+  if constexpr (SrcB::kAlongN) {
+    const int kpad = 2 * pb, tn = (npad + kSplitTile - 1) / kSplitTile, tk = (kpad + kSplitTile - 1) / kSplitTile;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = bblk; t < tn * tk; t += nbblk) {
+      const int n0 = (t % tn) * kSplitTile, k0 = (t / tn) * kSplitTile;
+#pragma unroll
+      for (int i = 0; i < kSplitTile / 8; ++i) {
+        const int kl = w + 8 * i, k = k0 + kl, n = n0 + lane;
+        bool ok = false;
+        float2 v = make_float2(0.f, 0.f);
+        if (k < Kb && n < npad) v = sb(k, n, ok);
+        tile[kl][lane] = ok ? v : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < (kSplitTile * kSplitTile / 2) / 256; ++i) {
+        const int item = (int)threadIdx.x + 256 * i;
+        const int nl = item / (kSplitTile / 2), kp = item % (kSplitTile / 2);
+        const int n = n0 + nl, k = k0 + 2 * kp;
+        if (n < npad && k < kpad) store_b_pair<M>(bhi, blo, ld, n, k, tile[2 * kp][nl], tile[2 * kp + 1][nl]);
+      }
+      __syncthreads();
+    }
+  } else {
+    const long long nb = (long long)npad * pb;
+    for (long long e = bblk * (long long)blockDim.x + threadIdx.x; e < nb; e += (long long)nbblk * blockDim.x) {
+      const int n = (int)(e / pb), k = 2 * (int)(e % pb);
       bool ok0 = false, ok1 = false;
       float2 v0 = make_float2(0.f, 0.f), v1 = v0;
       if (k < Kb) v0 = sb(k, n, ok0);
       if (k + 1 < Kb) v1 = sb(k + 1, n, ok1);
       if (!ok0) v0 = make_float2(0.f, 0.f);
       if (!ok1) v1 = make_float2(0.f, 0.f);
-      T hr0, lr0, hi0, li0, hn0, ln0, hr1, lr1, hi1, li1, hn1, ln1;
-      Split<M>::run(v0.x, hr0, lr0);
-      Split<M>::run(v0.y, hi0, li0);
-      Split<M>::run(-v0.y, hn0, ln0);
-      Split<M>::run(v1.x, hr1, lr1);
-      Split<M>::run(v1.y, hi1, li1);
-      Split<M>::run(-v1.y, hn1, ln1);
-      const size_t o0 = (size_t)(2 * n) * ld + 2 * k, o1 = o0 + ld;
-      Quad<M>::store(bhi + o0, hr0, hn0, hr1, hn1);
-      Quad<M>::store(bhi + o1, hi0, hr0, hi1, hr1);
-      Quad<M>::store(blo + o0, lr0, ln0, lr1, ln1);
-      Quad<M>::store(blo + o1, li0, lr0, li1, lr1);
+      store_b_pair<M>(bhi, blo, ld, n, k, v0, v1);
     }
   }
 }
@@ -293,11 +339,20 @@ __global__ void __launch_bounds__(256) split_ab_kernel(SrcA sa, SrcB sb, int ld,
 // tensor map with a 128-byte x 128-row box).  CTA (bx, by) computes rows
 // 128 by .. and logical complex columns 64 bx ..; the grid is sized for the
 // capacities and the epilogue functor's dims() gives the actual rows, real K
-// and logical columns (read from device memory).  Its call operator gets
-// (row, tile column base, acc, lane) with acc[2c + u] the component u of
-// complex column c of the tile (c < 64) for that row; rows r and r ^ 1 sit in
-// lanes l and l ^ 1 of one warp, for exchanges between neighbouring rows.
-// Every thread of the warp calls it (rows past the actual count included).
+// and logical columns (read from device memory).
+//
+// Epilogue functor interface (both calls made by every lane of a warp, rows
+// past the actual count included):
+//  * values(row, nbase, acc, v): from acc[2c + u] = component u of complex
+//    column nbase + c (c < 64) of this lane's row, the 64 complex outputs of
+//    the row, v[32 h + e] = entry e of output run h; rows r and r ^ 1 sit in
+//    lanes l and l ^ 1 of one warp, for exchanges between neighbouring rows;
+//  * run(row, nbase, h, count): where output run h of the row starts in
+//    global memory (32 consecutive complex values, of which the first count
+//    exist), or nullptr for a row past the actual count.
+// The epilogue warps stage their rows' outputs in the (then idle) pipeline
+// shared memory and write each run with consecutive lanes, so the stores
+// coalesce.
 template <int M, class Epi>
 __global__ void __launch_bounds__(kThreads, 1)
     cgemm_tma_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
@@ -402,7 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       bar_wait(&drained, 0, &never);
     }
   } else {
-    // ---- epilogue warps: drain chunk accumulators into FP32 registers
+    // ---- epilogue warps: drain group accumulators into FP32 registers
     const int quarter = warp & 3;  // tensor-memory lane quarter this warp may access
     const int row = m0 + quarter * 32 + lane;
     float acc[kBNr];
@@ -431,7 +486,28 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) bar_arrive(&tempty[b]);
     }
     ok = ok && !abort_s;
-    if (ok) epi(row, blockIdx.x * kBNc, acc, lane);
+    if (ok) {
+      // Every MMA has completed (the last group's commit), so the pipeline
+      // stages hold no operand still being read and every TMA copy has
+      // landed: each epilogue warp stages its 32 rows x 64 outputs there.
+      const int nbase = blockIdx.x * kBNc;
+      float2 v[64];
+      epi.values(row, nbase, acc, v);
+      constexpr int kPad = 65;  // row stride in complex values (conflict-light staging writes)
+      float2* stage = reinterpret_cast<float2*>(base) + (size_t)(warp - 2) * 32 * kPad;
+#pragma unroll
+      for (int e = 0; e < 64; ++e) stage[lane * kPad + e] = v[e];
+      __syncwarp();
+      for (int r = 0; r < 32; ++r) {
+        const int rr = m0 + quarter * 32 + r;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          int count = 0;
+          float2* dst = epi.run(rr, nbase, h, count);
+          if (dst != nullptr && lane < count) dst[lane] = stage[r * kPad + 32 * h + lane];
+        }
+      }
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
