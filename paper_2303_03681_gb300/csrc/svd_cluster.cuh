@@ -133,9 +133,10 @@ __device__ __forceinline__ int jacobi_pair_reg(cplx<S> (&x)[kClusterRegs], cplx<
 
 
 // Double-float forms of the two pair steps (FP64-accurate sweeps; the columns
-// hold float4 = (re_h, re_l, im_h, im_l)).  The Gram entries accumulate in
-// double-float per lane and across the warp; the rotation (an FP32 angle
-// brought to unit norm in FP64, jacobi_rotation<double>) is applied in
+// hold float4 = (re_h, re_l, im_h, im_l)).  The Gram entries accumulate per
+// lane as exact heads plus FP32 error terms (GramAcc) and in double-float
+// across the warp; the rotation (an FP32 angle
+// brought to unit norm in double-float, ff_angle) is applied in
 // double-float.
 __device__ __forceinline__ void ff_warp_sum4(ff& a, ff& b, ff& c, ff& d) {
 #pragma unroll
@@ -147,12 +148,36 @@ __device__ __forceinline__ void ff_warp_sum4(ff& a, ff& b, ff& c, ff& d) {
   }
 }
 
-__device__ __forceinline__ void ff_gram_row(const float4& x, const float4& y, ff& alpha, ff& beta, ff& gr, ff& gi) {
+// Per-lane Gram sums: a running FP32 head h, summed exactly (two_sum), and
+// an FP32 error term e collecting the two_sum errors and each product's
+// exact error (fma) and cross terms a_h b_l + a_l b_h.  A lane adds m / 32
+// products, so e's own rounding stays far below the stopping tolerance
+// (12 FP32 operations a product against 18 for a double-float fma).
+struct GramAcc {
+  float h = 0.f, e = 0.f;
+  __device__ __forceinline__ void add(ff a, ff b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float pe = __fmaf_rn(a.h, b.h, -p);
+    pe = __fmaf_rn(a.h, b.l, pe);
+    pe = __fmaf_rn(a.l, b.h, pe);
+    const ff s = two_sum(h, p);
+    h = s.h;
+    e = __fadd_rn(e, __fadd_rn(s.l, pe));
+  }
+  __device__ __forceinline__ ff value() const { return quick_two_sum(h, e); }
+};
+
+__device__ __forceinline__ void ff_gram_row(const float4& x, const float4& y, GramAcc& alpha, GramAcc& beta,
+                                            GramAcc& gr, GramAcc& gi) {
   const ff xr = re_of(x), xi = im_of(x), yr = re_of(y), yi = im_of(y);
-  alpha = ff_fma(xr, xr, ff_fma(xi, xi, alpha));
-  beta = ff_fma(yr, yr, ff_fma(yi, yi, beta));
-  gr = ff_fma(xr, yr, ff_fma(xi, yi, gr));
-  gi = ff_add(gi, ff_sub(ff_mul(xr, yi), ff_mul(xi, yr)));
+  alpha.add(xr, xr);
+  alpha.add(xi, xi);
+  beta.add(yr, yr);
+  beta.add(yi, yi);
+  gr.add(xr, yr);
+  gr.add(xi, yi);
+  gi.add(xr, yi);
+  gi.add(ff_neg(xi), yr);
 }
 
 // x' = c x - conj(s) y, y' = c y + s x with s = sr + i si
@@ -166,26 +191,75 @@ __device__ __forceinline__ void ff_rotate(float4& x, float4& y, ff c, ff sr, ff 
   y = cff(nyr, nyi);
 }
 
-__device__ __forceinline__ bool ff_angle(ff alpha, ff beta, ff gr, ff gi, double tol, double floor, double tiny, ff& c,
-                                         ff& sr, ff& si) {
-  double cd;
-  cplx<double> sph;
-  if (!jacobi_rotation<double>(ff_to_double(alpha), ff_to_double(beta), ff_to_double(gr), ff_to_double(gi), tol,
-                               floor, tiny, cd, sph))
-    return false;
-  c = ff_from_double(cd);
-  sr = ff_from_double(sph.x);
-  si = ff_from_double(sph.y);
+// 2^-e for the exponent e of a positive normal float x (x 2^-e in [1, 2)).
+__device__ __forceinline__ float pow2_inv_exponent(float x) {
+  const int e = ((__float_as_int(x) >> 23) & 0xff) - 127;
+  return __int_as_float((127 - e) << 23);
+}
+
+// The rotation of a pair from its double-float Gram entries, on the FP32
+// pipes only (this part runs FP64 at 2 FMA/clk/SM, and an FP64 angle for
+// every pair of 16 warps cost more than the rest of the pair step).  The
+// stopping test and the angle use FP32 values of the heads, scaled by a
+// power of two so that max(b_ii, b_jj) lies in [1, 2) (|g| is taken as a
+// scaled hypot, so no square underflows); b_jj - b_ii is formed in
+// double-float first, so the angle of a nearly degenerate pair is not
+// rounding noise.  The FP32 angle gives (c, s e^{i phi}) with c^2 + |s|^2 =
+// 1 + d, |d| ~ 2^-24; d is evaluated to ~2^-47 with exact products and sums
+// (two_prod, two_sum) and the rotation is scaled by f = 1 - d/2 + 3d^2/8
+// (the binomial series of (1 + d)^(-1/2)), which makes it unitary to
+// double-float rounding.  The angle itself is FP32-accurate: a pair left
+// with |g| ~ 1e-7 of its old value is rotated again in the next sweep.
+__device__ __forceinline__ ff two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return ff_make(p, __fmaf_rn(a, b, -p));
+}
+
+__device__ __forceinline__ bool ff_angle(ff alpha, ff beta, ff gr, ff gi, float tol, float floor, ff& c, ff& sr,
+                                         ff& si) {
+  const float a = alpha.h, b = beta.h;
+  if (!(fminf(a, b) > floor)) return false;
+  const float scl = pow2_inv_exponent(fmaxf(a, b));
+  const float xr = gr.h * scl, xi = gi.h * scl;  // |x| <= sqrt(a b) scl < 2
+  const float ax = fabsf(xr), ay = fabsf(xi);
+  const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+  if (!(mx > 0.f)) return false;
+  const float rr = mn / mx;
+  const float mag = mx * sqrtf(fmaf(rr, rr, 1.f));
+  if (!(mag > tol * sqrtf(a * scl) * sqrtf(b * scl))) return false;
+  const ff dba = ff_sub(beta, alpha);
+  const float zeta = (dba.h * scl) / (2.f * mag);
+  if (!(fabsf(zeta) < 3e38f)) return false;
+  const float t = fabsf(zeta) > 1e15f ? 0.5f / zeta
+                                       : copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+  const float cf = rsqrtf(fmaf(t, t, 1.f));
+  const float sf = t * cf / mag;
+  // s e^{i phi} = sf (xr + i xi), exact as double-float
+  const ff s_r = two_prod(sf, xr), s_i = two_prod(sf, xi);
+  // d = c^2 + |s|^2 - 1 with exact products and sums of the heads (cf^2
+  // can round just below 1/2, so even cf^2 - 1 goes through two_sum)
+  const ff c2 = two_prod(cf, cf), r2 = two_prod(s_r.h, s_r.h), i2 = two_prod(s_i.h, s_i.h);
+  const ff u0 = two_sum(c2.h, -1.f);
+  const ff u1 = two_sum(u0.h, r2.h);
+  const ff u2 = two_sum(u1.h, i2.h);
+  const float tail = __fadd_rn(__fadd_rn(__fadd_rn(u0.l, u1.l), u2.l), __fadd_rn(c2.l, __fadd_rn(r2.l, i2.l)));
+  const float cross = 2.f * __fmaf_rn(s_r.h, s_r.l, __fmul_rn(s_i.h, s_i.l));
+  const float d = __fadd_rn(u2.h, __fadd_rn(tail, cross));
+  const float fl = __fmaf_rn(0.375f * d, d, -0.5f * d);  // f = 1 + fl
+  c = quick_two_sum(cf, __fmul_rn(cf, fl));
+  sr = quick_two_sum(s_r.h, __fmaf_rn(s_r.h, fl, s_r.l));
+  si = quick_two_sum(s_i.h, __fmaf_rn(s_i.h, fl, s_i.l));
   return true;
 }
 
 __device__ __forceinline__ int ff_pair_smem(float4* ai, float4* aj, int m, int len, int lane, double tol, double floor,
                                             double tiny) {
-  ff alpha = ff_make(0.f, 0.f), beta = alpha, gr = alpha, gi = alpha;
-  for (int r = lane; r < m; r += 32) ff_gram_row(ai[r], aj[r], alpha, beta, gr, gi);
+  GramAcc ga, gb, gc, gd;
+  for (int r = lane; r < m; r += 32) ff_gram_row(ai[r], aj[r], ga, gb, gc, gd);
+  ff alpha = ga.value(), beta = gb.value(), gr = gc.value(), gi = gd.value();
   ff_warp_sum4(alpha, beta, gr, gi);
   ff c, sr, si;
-  if (!ff_angle(alpha, beta, gr, gi, tol, floor, tiny, c, sr, si)) return 0;
+  if (!ff_angle(alpha, beta, gr, gi, float(tol), float(floor), c, sr, si)) return 0;
   for (int r = lane; r < len; r += 32) {
     float4 x = ai[r], y = aj[r];
     ff_rotate(x, y, c, sr, si);
@@ -197,15 +271,16 @@ __device__ __forceinline__ int ff_pair_smem(float4* ai, float4* aj, int m, int l
 
 __device__ __forceinline__ int ff_pair_reg(float4 (&x)[kClusterRegs], float4* aj, int m, int len, int lane,
                                            double tol, double floor, double tiny) {
-  ff alpha = ff_make(0.f, 0.f), beta = alpha, gr = alpha, gi = alpha;
+  GramAcc ga, gb, gc, gd;
 #pragma unroll
   for (int i = 0; i < kClusterRegs; ++i) {
     const int r = lane + 32 * i;
-    if (r < m) ff_gram_row(x[i], aj[r], alpha, beta, gr, gi);
+    if (r < m) ff_gram_row(x[i], aj[r], ga, gb, gc, gd);
   }
+  ff alpha = ga.value(), beta = gb.value(), gr = gc.value(), gi = gd.value();
   ff_warp_sum4(alpha, beta, gr, gi);
   ff c, sr, si;
-  if (!ff_angle(alpha, beta, gr, gi, tol, floor, tiny, c, sr, si)) return 0;
+  if (!ff_angle(alpha, beta, gr, gi, float(tol), float(floor), c, sr, si)) return 0;
 #pragma unroll
   for (int i = 0; i < kClusterRegs; ++i) {
     const int r = lane + 32 * i;
@@ -301,12 +376,23 @@ struct ColStore {
 // the columns the truncation discards (truncation_tail, into tail[]); a pair
 // of two marked columns is not rotated.
 //
+// Clean pairs (kOp 0): a pair whose two columns have not changed since the
+// pair was last tested at the tight tolerance, and found orthogonal, is
+// orthogonal still; it is not tested again.  Byte flags per column id, kept
+// identical in every member CTA: dirty[] (rotated in this sweep; a rotation
+// sets both columns' flags in every member CTA through distributed shared
+// memory, visible by the next round's cluster barrier), dirty_prev[] (rotated
+// in the previous sweep) and tight_prev[] (tail class 0 in the previous
+// sweep).  A pair is clean when both columns are tight now and were in the
+// previous sweep, and neither was rotated in the previous sweep or so far in
+// this one.  The first sweep tests every pair.
+//
 // kDF: the columns hold double-float values (float4, see dfloat.cuh) and the
 // rotations run in double-float; T is double then.
 template <typename T, int kOp, bool kGlobal, bool kDF = false>
 __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColStore<T, kGlobal>& cs, int& cur, int max_sweeps, T tol, T floor,
-                              T tiny, double trunc_rel, int chi_max, double* nrm2, int* tail, bool& converged,
-                              const cg::cluster_group& cluster, int* s_flag_in, int* s_any) {
+                              T tiny, double trunc_rel, int chi_max, double* nrm2, int* tail, unsigned char* flags,
+                              bool& converged, const cg::cluster_group& cluster, int* s_flag_in, int* s_any) {
   using C = cplx<T>;
   using E = std::conditional_t<kDF, float4, C>;  // a stored entry
   static_assert(!kDF || (sizeof(float4) == sizeof(C) && kOp == 0), "double-float columns replace complex128 ones");
@@ -318,6 +404,31 @@ __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColSto
   __shared__ double s_loose;
   T loose = T(0);  // the tail rule's loose tolerance of the sweep (pair_tol)
   const bool active = g.member && g.wp < g.b;
+  unsigned char* dirty = flags;
+  unsigned char* dirty_prev = flags + g.ncols_pad;
+  unsigned char* tight_prev = flags + 2 * g.ncols_pad;
+  if (kOp == 0) {
+    for (int id = threadIdx.x; id < g.ncols_pad; id += g.nt) {
+      dirty[id] = 0;
+      dirty_prev[id] = 1;
+      tight_prev[id] = 0;
+    }
+    __syncthreads();
+  }
+  // a pair (column ids i, j) that needs no test (see above)
+  auto clean = [&](int i, int j) -> bool {
+    return tail[i] == 0 && tail[j] == 0 && tight_prev[i] && tight_prev[j] && !(dirty_prev[i] | dirty_prev[j] |
+                                                                               dirty[i] | dirty[j]);
+  };
+  // both columns rotated: flag them in every member CTA (lane 0 of the warp)
+  auto mark = [&](int i, int j) {
+    if (g.wl != 0) return;
+    for (int r2 = 0; r2 < g.P; ++r2) {
+      unsigned char* d = r2 == g.me ? dirty : cluster.map_shared_rank(dirty, r2);
+      d[i] = 1;
+      d[j] = 1;
+    }
+  };
   int sweep = 0;
   converged = false;
   for (; sweep < max_sweeps; ++sweep) {
@@ -360,14 +471,17 @@ __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColSto
             C* x = cs.col(cur, a0 / g.b, a0 % g.b, rnd);
             C* y = cs.col(cur, a1 / g.b, a1 % g.b, rnd);
             if (kOp == 0) {
-              const T tl = pair_tol(tail[col_id(g, a0 / g.b, a0 % g.b, rnd)], tail[col_id(g, a1 / g.b, a1 % g.b, rnd)],
-                                    tol, loose);
-              if (tl >= T(0)) {
+              const int i0 = col_id(g, a0 / g.b, a0 % g.b, rnd), i1 = col_id(g, a1 / g.b, a1 % g.b, rnd);
+              const T tl = pair_tol(tail[i0], tail[i1], tol, loose);
+              if (tl >= T(0) && !clean(i0, i1)) {
+                int r;
                 if constexpr (kDF)
-                  rotated |= ff_pair_smem(reinterpret_cast<float4*>(x), reinterpret_cast<float4*>(y), g.m, g.len,
-                                          g.wl, tl, floor, tiny);
+                  r = ff_pair_smem(reinterpret_cast<float4*>(x), reinterpret_cast<float4*>(y), g.m, g.len, g.wl, tl,
+                                   floor, tiny);
                 else
-                  rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tl, floor, tiny);
+                  r = jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tl, floor, tiny);
+                if (r) mark(i0, i1);
+                rotated |= r;
               }
             } else
               orth_pair<T>(x, y, g.m, g.len, g.wl);
@@ -390,15 +504,18 @@ __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColSto
         for (int sr = 0; sr < g.b; ++sr) {
           if (cache_x) {
             if (active) {
-              const T tl = pair_tol(tail[col_id(g, 0, g.wp, rnd)], tail[col_id(g, 1, (g.wp + sr) % g.b, rnd)], tol,
-                                    loose);
-              if (tl >= T(0)) {
+              const int i0 = col_id(g, 0, g.wp, rnd), i1 = col_id(g, 1, (g.wp + sr) % g.b, rnd);
+              const T tl = pair_tol(tail[i0], tail[i1], tol, loose);
+              if (tl >= T(0) && !clean(i0, i1)) {
+                int r;
                 if constexpr (kDF)
-                  rotated |= ff_pair_reg(xr, reinterpret_cast<float4*>(cs.col(cur, 1, (g.wp + sr) % g.b, rnd)), g.m,
-                                         g.len, g.wl, tl, floor, tiny);
+                  r = ff_pair_reg(xr, reinterpret_cast<float4*>(cs.col(cur, 1, (g.wp + sr) % g.b, rnd)), g.m, g.len,
+                                  g.wl, tl, floor, tiny);
                 else
-                  rotated |= jacobi_pair_reg<T>(xr, cs.col(cur, 1, (g.wp + sr) % g.b, rnd), g.m, g.len, g.wl, tl,
-                                                floor, tiny);
+                  r = jacobi_pair_reg<T>(xr, cs.col(cur, 1, (g.wp + sr) % g.b, rnd), g.m, g.len, g.wl, tl, floor,
+                                         tiny);
+                if (r) mark(i0, i1);
+                rotated |= r;
               }
             }
           } else {
@@ -406,14 +523,17 @@ __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColSto
               C* x = cs.col(cur, 0, pw, rnd);
               C* y = cs.col(cur, 1, (pw + sr) % g.b, rnd);
               if (kOp == 0) {
-                const T tl = pair_tol(tail[col_id(g, 0, pw, rnd)], tail[col_id(g, 1, (pw + sr) % g.b, rnd)], tol,
-                                      loose);
-                if (tl >= T(0)) {
+                const int i0 = col_id(g, 0, pw, rnd), i1 = col_id(g, 1, (pw + sr) % g.b, rnd);
+                const T tl = pair_tol(tail[i0], tail[i1], tol, loose);
+                if (tl >= T(0) && !clean(i0, i1)) {
+                  int r;
                   if constexpr (kDF)
-                    rotated |= ff_pair_smem(reinterpret_cast<float4*>(x), reinterpret_cast<float4*>(y), g.m, g.len,
-                                            g.wl, tl, floor, tiny);
+                    r = ff_pair_smem(reinterpret_cast<float4*>(x), reinterpret_cast<float4*>(y), g.m, g.len, g.wl,
+                                     tl, floor, tiny);
                   else
-                    rotated |= jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tl, floor, tiny);
+                    r = jacobi_pair_smem<T>(x, y, g.m, g.len, g.wl, tl, floor, tiny);
+                  if (r) mark(i0, i1);
+                  rotated |= r;
                 }
               } else
                 orth_pair<T>(x, y, g.m, g.len, g.wl);
@@ -464,6 +584,14 @@ __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColSto
     int any = 0;
     for (int r2 = 0; r2 < g.Pl; ++r2) any |= s_flag_in[r2];
     cluster.sync();  // all reads done before the next sweep's writes
+    // roll the clean-pair flags (no CTA writes dirty[] again before the next
+    // sweep's norm exchange barrier)
+    for (int id = threadIdx.x; g.member && id < g.ncols_pad; id += g.nt) {
+      dirty_prev[id] = dirty[id];
+      dirty[id] = 0;
+      tight_prev[id] = tail[id] == 0;
+    }
+    __syncthreads();
     if (!any) {
       converged = true;
       ++sweep;
@@ -481,7 +609,7 @@ template <typename S> constexpr int kClusterMaxThreads = sizeof(S) == 8 ? 256 : 
 template <typename S>
 struct ClusterSvdSmem {
   // layout of the dynamic shared memory (offsets in bytes); len = m + n
-  size_t buf, red, sig, rank;
+  size_t buf, red, sig, rank, flags;
   size_t total;
   __host__ __device__ static size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
   __host__ __device__ ClusterSvdSmem(int b, int len, int ncols_pad, int nthreads) {
@@ -490,7 +618,8 @@ struct ClusterSvdSmem {
     red = align16(buf + slots);
     sig = align16(red + 4ull * (nthreads / 32 + 1) * sizeof(S) * 2);
     rank = align16(sig + (size_t)ncols_pad * sizeof(double));
-    total = align16(rank + (size_t)ncols_pad * sizeof(int)) + 64;
+    flags = align16(rank + (size_t)ncols_pad * sizeof(int));  // three byte flags per column
+    total = align16(flags + 3 * (size_t)ncols_pad) + 64;
   }
 };
 
@@ -582,6 +711,7 @@ __device__ __forceinline__ void svd_cluster_body(const ClusterGeom& g, const cg:
   // columns (the singular values and ranks use the same arrays afterwards)
   double* nrm2 = sig;
   int* tail = rnk;
+  unsigned char* flags = smem + L.flags;
   int cur = 0, used = 0, used32 = 0;
   bool converged = false;
   t_load = clock64();
@@ -592,7 +722,7 @@ __device__ __forceinline__ void svd_cluster_body(const ClusterGeom& g, const cg:
     bool conv32 = false;
     used32 = cluster_sweeps<float, 0, kGlobal>(g, cs32, cur32, p.max_sweeps, float(tol_scale) * u32,
                                                float(16.0 * double(u32) * double(u32) * fro2), 1e-35f, p.trunc_rel,
-                                               p.chi_max, nrm2, tail, conv32, cluster, s_flag_in, s_any);
+                                               p.chi_max, nrm2, tail, flags, conv32, cluster, s_flag_in, s_any);
     used = used32;
     t_lo = clock64();
     // FP64 columns: V promoted (A follows from the theta below)
@@ -610,8 +740,8 @@ __device__ __forceinline__ void svd_cluster_body(const ClusterGeom& g, const cg:
     // unitary only to ~1e-10 after long FP32 phases)
     for (int pass = 0; pass < 2; ++pass) {
       bool dummy;
-      cluster_sweeps<S, 1, kGlobal>(g, cs, cur, 1, S(0), S(0), S(0), 0.0, 0, nrm2, tail, dummy, cluster, s_flag_in,
-                                    s_any);
+      cluster_sweeps<S, 1, kGlobal>(g, cs, cur, 1, S(0), S(0), S(0), 0.0, 0, nrm2, tail, flags, dummy, cluster,
+                                    s_flag_in, s_any);
       // the diagonal of the first-order step: |v|^2 -> 1
       for (int c = g.wp; g.member && c < 2 * b; c += g.nw) {
         C* v = cs.col(cur, c / b, c % b, 0);
@@ -659,7 +789,7 @@ __device__ __forceinline__ void svd_cluster_body(const ClusterGeom& g, const cg:
   const S floor = S(16.0 * double(eps_u) * double(eps_u) * fro2);
   const S tiny = sizeof(S) == 8 ? S(1e-290) : S(1e-35f);
   used += cluster_sweeps<S, 0, kGlobal, kDF>(g, cs, cur, p.max_sweeps, tol, floor, tiny, p.trunc_rel, p.chi_max, nrm2, tail,
-                                        converged, cluster, s_flag_in, s_any);
+                                        flags, converged, cluster, s_flag_in, s_any);
   const int sweep = used;
 
   // ---- singular values: norms of the A parts, shared with every CTA
