@@ -406,14 +406,14 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "c128" if w["precision"] == "fp64" else "c64",
         "data": "synthetic",
         "config": dict(w["desc"], precision=({"fp32": "complex64 storage and contractions, ",
-                                              "fp64": "complex128 storage and contractions, ",
+                                              "fp64": "complex128 storage, double-float contractions, ",
                                               "tf32x3": "complex64 storage, TF32x3 tensor-core contractions, ",
                                               "bf16x3": "complex64 storage, BF16x3 tensor-core contractions, ",
                                               "auto": "complex64 storage, TF32x3 contractions at capacity >= 256, "}
                                              [w["precision"]]
                                              + {"fp32": "FP32 Jacobi SVD",
                                                 "fp64": ("FP64-accurate Jacobi SVD (FP32 sweeps, FP64 "
-                                                         "re-orthonormalisation, FP64 sweeps)"),
+                                                         "re-orthonormalisation, double-float sweeps)"),
                                                 "fp64-all": "FP64 Jacobi SVD"}[args.svd]
                                              + ", FP64 energy sum"),
                        contractions=contraction_label(args, w, reps),
@@ -718,7 +718,7 @@ def contraction_label(args, w, reps):
     environment path serves complex64 states at bond dimension >= 64 only, the
     split-product gate contractions the TF32X3 / BF16X3 / AUTO modes."""
     if w["precision"] == "fp64":
-        return "CUDA cores (FP64)"
+        return "CUDA cores (double-float on the FP32 units, complex128 in memory)"
     gates = {"fp32": "gates on CUDA cores (FP32)", "tf32x3": "gates on tcgen05 (TMA, TF32x3)",
              "bf16x3": "gates on tcgen05 (TMA, BF16x3)", "auto": "gates on tcgen05 (TMA, TF32x3) at capacity >= 256"}
     gates = gates[w["precision"]]

@@ -54,8 +54,13 @@ typedef enum {
   MPS_ESTATE = 7      /* state left inconsistent by an earlier failure: reset it */
 } mps_status;
 
-/* Arithmetic of a state.  The truncation SVD and the energy sum are FP64 in
- * every mode unless mps_config.svd_fp64 = 0.  The split-product modes keep
+/* Arithmetic of a state.  The truncation SVD is FP64-accurate and the energy
+ * sum FP64 in every mode unless mps_config.svd_fp64 = 0.  MPS_PREC_FP64
+ * stores complex128; its CUDA-core contractions (theta, B~_q, environments)
+ * and the FP64-accurate Jacobi sweeps compute in double-float arithmetic
+ * (pairs of FP32 values, about 2^-46 relative per operation) on the FP32
+ * units, since this part executes FP64 at 1/64 of the FP32 rate; results
+ * are stored as complex128.  The split-product modes keep
  * complex64 storage and run the theta contraction C = Q (B_q B_{q+1}) and
  * B~_q = C V^dagger (Eqs. tildeC, Bl) as tensor-core GEMMs (tcgen05, operands
  * loaded with TMA) in which every real operand value is split into two
@@ -64,7 +69,7 @@ typedef enum {
  * contractions use the tensor cores at bond dimension >= 64 as
  * mps_config.tensor_cores does. */
 typedef enum {
-  MPS_PREC_FP64 = 0,   /* complex128 storage, FP64 contractions */
+  MPS_PREC_FP64 = 0,   /* complex128 storage, double-float contractions */
   MPS_PREC_FP32 = 1,   /* complex64 storage, FP32 CUDA-core contractions */
   MPS_PREC_BF16X3 = 2, /* complex64 storage, BF16 pieces (16 bits of each value kept) */
   MPS_PREC_TF32X3 = 3, /* complex64 storage, TF32 pieces (22 bits kept: about FP32 accuracy) */

@@ -65,6 +65,12 @@ __device__ __forceinline__ ff ff_mul(ff a, ff b) {
 // acc + a b
 __device__ __forceinline__ ff ff_fma(ff a, ff b, ff acc) { return ff_add(ff_mul(a, b), acc); }
 
+// exact: h + l = a b (the fma two-product)
+__device__ __forceinline__ ff two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return ff_make(p, __fmaf_rn(a, b, -p));
+}
+
 __device__ __forceinline__ ff ff_from_double(double x) {
   const float h = __double2float_rn(x);
   return ff_make(h, __double2float_rn(x - (double)h));
@@ -89,5 +95,50 @@ __device__ __forceinline__ float4 cff_from_double2(double2 z) {
 __device__ __forceinline__ double2 cff_to_double2(const float4& z) {
   return make_double2(ff_to_double(re_of(z)), ff_to_double(im_of(z)));
 }
+
+// Sums of double-float products (the per-lane Gram sums of the Jacobi SVD,
+// the multiply-adds of the complex128 contractions): a running FP32 head h,
+// summed exactly (two_sum), and an FP32 error term e collecting the two_sum
+// errors and each product's exact error (fma) and cross terms a_h b_l +
+// a_l b_h; 12 FP32 operations a product against 18 for a double-float fma.
+// e holds about 2^-23 of the sum of |products|, so after K additions its
+// own rounding is about K 2^-47 of that sum (1e-12 at K = 128).
+struct GramAcc {
+  float h = 0.f, e = 0.f;
+  __device__ __forceinline__ void add(ff a, ff b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float pe = __fmaf_rn(a.h, b.h, -p);
+    pe = __fmaf_rn(a.h, b.l, pe);
+    pe = __fmaf_rn(a.l, b.h, pe);
+    const ff s = two_sum(h, p);
+    h = s.h;
+    e = __fadd_rn(e, __fadd_rn(s.l, pe));
+  }
+  __device__ __forceinline__ ff value() const { return quick_two_sum(h, e); }
+};
+
+// Complex multiply-adds on double-float operands into a pair of GramAcc.
+struct CAcc {
+  GramAcc re, im;
+  // += a b
+  __device__ __forceinline__ void fma(const float4& a, const float4& b) {
+    const ff ar = re_of(a), ai = im_of(a), br = re_of(b), bi = im_of(b);
+    re.add(ar, br);
+    re.add(ff_neg(ai), bi);
+    im.add(ar, bi);
+    im.add(ai, br);
+  }
+  // += conj(a) b
+  __device__ __forceinline__ void fmac(const float4& a, const float4& b) {
+    const ff ar = re_of(a), ai = im_of(a), br = re_of(b), bi = im_of(b);
+    re.add(ar, br);
+    re.add(ai, bi);
+    im.add(ar, bi);
+    im.add(ff_neg(ai), br);
+  }
+  __device__ __forceinline__ double2 value() const {
+    return make_double2(ff_to_double(re.value()), ff_to_double(im.value()));
+  }
+};
 
 }  // namespace mpsv

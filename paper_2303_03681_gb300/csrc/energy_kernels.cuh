@@ -18,6 +18,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "gate_kernels.cuh"  // kTile, Mac
 
 namespace mpsv {
 
@@ -78,28 +79,30 @@ __global__ void __launch_bounds__(kTile* kTile)
     }
     return;
   }
+  using MT = Mac<R>;
+  using E = typename MT::Elem;
   const C* L = Lprev + (size_t)src * lv.cap_l * lv.cap_l;
-  __shared__ C sL[kTile][kTile + 1];
-  __shared__ C sB[2][kTile][kTile + 1];
-  C acc0 = zero, acc1 = zero;
+  __shared__ E sL[kTile][kTile + 1];
+  __shared__ E sB[2][kTile][kTile + 1];
+  typename MT::Acc acc0, acc1;
   for (int c0 = 0; c0 < chi_l; c0 += kTile) {
-    sL[ty][tx] = (a < chi_l && c0 + tx < chi_l) ? L[(size_t)a * chi_l + c0 + tx] : zero;
+    sL[ty][tx] = (a < chi_l && c0 + tx < chi_l) ? MT::load(L[(size_t)a * chi_l + c0 + tx]) : MT::zero();
     const int c = c0 + ty;
     const bool ok = c < chi_l && d < chi_r;
-    sB[0][ty][tx] = ok ? B[(size_t)(c * 2 + 0) * chi_r + d] : zero;
-    sB[1][ty][tx] = ok ? B[(size_t)(c * 2 + 1) * chi_r + d] : zero;
+    sB[0][ty][tx] = ok ? MT::load(B[(size_t)(c * 2 + 0) * chi_r + d]) : MT::zero();
+    sB[1][ty][tx] = ok ? MT::load(B[(size_t)(c * 2 + 1) * chi_r + d]) : MT::zero();
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < kTile; ++kk) {
-      const C l = sL[ty][kk];
-      cfma(acc0, l, sB[0][kk][tx]);
-      cfma(acc1, l, sB[1][kk][tx]);
+      const E l = sL[ty][kk];
+      MT::fma(acc0, l, sB[0][kk][tx]);
+      MT::fma(acc1, l, sB[1][kk][tx]);
     }
     __syncthreads();
   }
   if (a < chi_l && d < chi_r) {
-    out[(size_t)a * 2 * chi_r + d] = acc0;
-    out[(size_t)a * 2 * chi_r + chi_r + d] = acc1;
+    out[(size_t)a * 2 * chi_r + d] = MT::value(acc0);
+    out[(size_t)a * 2 * chi_r + chi_r + d] = MT::value(acc1);
   }
 }
 
@@ -122,30 +125,31 @@ __global__ void __launch_bounds__(kTile* kTile)
   const C* M1 = Mp + (size_t)pr.p1 * chi_r;  // partner of row i = 1
   const int tx = threadIdx.x, ty = threadIdx.y;
   const int b = b0 + ty, d = d0 + tx;
-  const C zero = cmk<R>(0, 0);
-  __shared__ C sB[2][kTile][kTile + 1];  // [i][a][b]
-  __shared__ C sM[2][kTile][kTile + 1];  // [i][a][d]
-  C acc0 = zero, acc1 = zero;
+  using MT = Mac<R>;
+  using E = typename MT::Elem;
+  __shared__ E sB[2][kTile][kTile + 1];  // [i][a][b]
+  __shared__ E sM[2][kTile][kTile + 1];  // [i][a][d]
+  typename MT::Acc acc0, acc1;
   for (int a0 = 0; a0 < chi_l; a0 += kTile) {
     const int a = a0 + ty;
     const int bb = b0 + tx;
     const bool okb = a < chi_l && bb < chi_r;
-    sB[0][ty][tx] = okb ? B[(size_t)(a * 2 + 0) * chi_r + bb] : zero;
-    sB[1][ty][tx] = okb ? B[(size_t)(a * 2 + 1) * chi_r + bb] : zero;
+    sB[0][ty][tx] = okb ? MT::load(B[(size_t)(a * 2 + 0) * chi_r + bb]) : MT::zero();
+    sB[1][ty][tx] = okb ? MT::load(B[(size_t)(a * 2 + 1) * chi_r + bb]) : MT::zero();
     const bool okm = a < chi_l && d < chi_r;
-    sM[0][ty][tx] = okm ? M0[(size_t)a * 2 * chi_r + d] : zero;
-    sM[1][ty][tx] = okm ? M1[(size_t)a * 2 * chi_r + d] : zero;
+    sM[0][ty][tx] = okm ? MT::load(M0[(size_t)a * 2 * chi_r + d]) : MT::zero();
+    sM[1][ty][tx] = okm ? MT::load(M1[(size_t)a * 2 * chi_r + d]) : MT::zero();
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < kTile; ++kk) {
-      cfmac(acc0, sB[0][kk][ty], sM[0][kk][tx]);
-      cfmac(acc1, sB[1][kk][ty], sM[1][kk][tx]);
+      MT::fmac(acc0, sB[0][kk][ty], sM[0][kk][tx]);
+      MT::fmac(acc1, sB[1][kk][ty], sM[1][kk][tx]);
     }
     __syncthreads();
   }
   if (b < chi_r && d < chi_r) {
-    C out = cmul(ccast<C>(pr.ph0), acc0);
-    out = cadd(out, cmul(ccast<C>(pr.ph1), acc1));
+    C out = cmul(ccast<C>(pr.ph0), MT::value(acc0));
+    out = cadd(out, cmul(ccast<C>(pr.ph1), MT::value(acc1)));
     Lcur[(size_t)cidx * lv.cap_r * lv.cap_r + (size_t)b * chi_r + d] = out;
   }
 }

@@ -15,10 +15,41 @@
 #pragma once
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace mpsv {
 
 constexpr int kTile = 16;
+
+// Tile elements and accumulators of the CUDA-core complex contractions
+// (theta, G3, the environments).  Complex64 states multiply-add in FP32.
+// Complex128 states hold their shared-memory tiles as double-float values
+// (converted once per tile load) and accumulate with exact heads plus FP32
+// error terms (CAcc) on the FP32 pipes: this part executes FP64 at 2 FMA
+// per clock per SM against 128 FP32, and a double-float multiply-add costs
+// 12 FP32 operations per real product (relative error about K 2^-47 of the
+// sum of |terms| for K products, 1e-12 at K = 128).
+template <typename R> struct Mac;
+template <> struct Mac<float> {
+  using Elem = float2;
+  struct Acc {
+    float2 v = make_float2(0.f, 0.f);
+  };
+  static __device__ __forceinline__ Elem load(float2 x) { return x; }
+  static __device__ __forceinline__ Elem zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ void fma(Acc& a, Elem x, Elem y) { cfma(a.v, x, y); }    // += x y
+  static __device__ __forceinline__ void fmac(Acc& a, Elem x, Elem y) { cfmac(a.v, x, y); }  // += conj(x) y
+  static __device__ __forceinline__ float2 value(const Acc& a) { return a.v; }
+};
+template <> struct Mac<double> {
+  using Elem = float4;
+  using Acc = CAcc;
+  static __device__ __forceinline__ Elem load(double2 x) { return cff_from_double2(x); }
+  static __device__ __forceinline__ Elem zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ void fma(Acc& a, Elem x, Elem y) { a.fma(x, y); }
+  static __device__ __forceinline__ void fmac(Acc& a, Elem x, Elem y) { a.fmac(x, y); }
+  static __device__ __forceinline__ double2 value(const Acc& a) { return a.value(); }
+};
 
 // ---------------------------------------------------------------------------
 // reset to a computational basis state (chi = 1 everywhere)
@@ -64,40 +95,38 @@ __global__ void __launch_bounds__(kTile* kTile)
                  const DevGate* __restrict__ gate, const double* __restrict__ lam_l,
                  const int* __restrict__ chi, int q, cplx<R>* __restrict__ Cm, cplx<S>* __restrict__ A) {
   using C = cplx<R>;
+  using MT = Mac<R>;
+  using E = typename MT::Elem;
   const int chi_l = chi[q], chi_m = chi[q + 1], chi_r = chi[q + 2];
   const int al0 = blockIdx.y * kTile, ar0 = blockIdx.x * kTile;
   if (al0 >= chi_l || ar0 >= chi_r) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  __shared__ C sL[2][kTile][kTile + 1];
-  __shared__ C sR[2][kTile][kTile + 1];
-  C acc[2][2];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) acc[i][j] = cmk<R>(0, 0);
+  __shared__ E sL[2][kTile][kTile + 1];
+  __shared__ E sR[2][kTile][kTile + 1];
+  typename MT::Acc acc[2][2];
   const C zero = cmk<R>(0, 0);
   for (int m0 = 0; m0 < chi_m; m0 += kTile) {
     {
       const int al = al0 + ty, mm = m0 + tx;
       const bool ok = al < chi_l && mm < chi_m;
-      sL[0][ty][tx] = ok ? Bl[(size_t)(al * 2 + 0) * chi_m + mm] : zero;
-      sL[1][ty][tx] = ok ? Bl[(size_t)(al * 2 + 1) * chi_m + mm] : zero;
+      sL[0][ty][tx] = ok ? MT::load(Bl[(size_t)(al * 2 + 0) * chi_m + mm]) : MT::zero();
+      sL[1][ty][tx] = ok ? MT::load(Bl[(size_t)(al * 2 + 1) * chi_m + mm]) : MT::zero();
     }
     {
       const int mm = m0 + ty, ar = ar0 + tx;
       const bool ok = mm < chi_m && ar < chi_r;
-      sR[0][ty][tx] = ok ? Br[(size_t)(mm * 2 + 0) * chi_r + ar] : zero;
-      sR[1][ty][tx] = ok ? Br[(size_t)(mm * 2 + 1) * chi_r + ar] : zero;
+      sR[0][ty][tx] = ok ? MT::load(Br[(size_t)(mm * 2 + 0) * chi_r + ar]) : MT::zero();
+      sR[1][ty][tx] = ok ? MT::load(Br[(size_t)(mm * 2 + 1) * chi_r + ar]) : MT::zero();
     }
     __syncthreads();
 #pragma unroll 4
     for (int kk = 0; kk < kTile; ++kk) {
-      const C l0 = sL[0][ty][kk], l1 = sL[1][ty][kk];
-      const C r0 = sR[0][kk][tx], r1 = sR[1][kk][tx];
-      cfma(acc[0][0], l0, r0);
-      cfma(acc[0][1], l0, r1);
-      cfma(acc[1][0], l1, r0);
-      cfma(acc[1][1], l1, r1);
+      const E l0 = sL[0][ty][kk], l1 = sL[1][ty][kk];
+      const E r0 = sR[0][kk][tx], r1 = sR[1][kk][tx];
+      MT::fma(acc[0][0], l0, r0);
+      MT::fma(acc[0][1], l0, r1);
+      MT::fma(acc[1][0], l1, r0);
+      MT::fma(acc[1][1], l1, r1);
     }
     __syncthreads();
   }
@@ -105,6 +134,11 @@ __global__ void __launch_bounds__(kTile* kTile)
   if (al >= chi_l || ar >= chi_r) return;
   const int m = 2 * chi_l, n = 2 * chi_r;
   const double lam = lam_l[al];
+  C th[2][2];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) th[i][j] = MT::value(acc[i][j]);
 #pragma unroll
   for (int i = 0; i < 2; ++i) {
 #pragma unroll
@@ -113,7 +147,7 @@ __global__ void __launch_bounds__(kTile* kTile)
 #pragma unroll
       for (int ip = 0; ip < 2; ++ip)
 #pragma unroll
-        for (int jp = 0; jp < 2; ++jp) cfma(out, ccast<C>(gate->u[(2 * i + j) * 4 + 2 * ip + jp]), acc[ip][jp]);
+        for (int jp = 0; jp < 2; ++jp) cfma(out, ccast<C>(gate->u[(2 * i + j) * 4 + 2 * ip + jp]), th[ip][jp]);
       const int row = 2 * al + i, col = j * chi_r + ar;
       Cm[(size_t)row * n + col] = out;
       if (A) {
@@ -372,28 +406,30 @@ __global__ void __launch_bounds__(kTile* kTile)
     g3_kernel(const cplx<R>* __restrict__ Cm, const cplx<R>* __restrict__ Bn, const int* __restrict__ chi, int q,
               const DevReport* __restrict__ rep, cplx<R>* __restrict__ Bout) {
   using C = cplx<R>;
+  using MT = Mac<R>;
+  using E = typename MT::Elem;
   const int chi_l = chi[q], k = chi[q + 1], chi_r = chi[q + 2];
   const int m = 2 * chi_l, n = 2 * chi_r;
   const int r0 = blockIdx.y * kTile, a0 = blockIdx.x * kTile;
   if (r0 >= m || a0 >= k) return;
   const int tx = threadIdx.x, ty = threadIdx.y;
-  __shared__ C sA[kTile][kTile + 1];
-  __shared__ C sB[kTile][kTile + 1];
-  const C zero = cmk<R>(0, 0);
-  C acc = zero;
+  __shared__ E sA[kTile][kTile + 1];
+  __shared__ E sB[kTile][kTile + 1];  // conj(B~_{q+1})
+  typename MT::Acc acc;
   for (int c0 = 0; c0 < n; c0 += kTile) {
     const int c = c0 + tx;
-    sA[ty][tx] = (r0 + ty < m && c < n) ? Cm[(size_t)(r0 + ty) * n + c] : zero;
-    sB[ty][tx] = (a0 + ty < k && c < n) ? Bn[(size_t)(a0 + ty) * n + c] : zero;
+    sA[ty][tx] = (r0 + ty < m && c < n) ? MT::load(Cm[(size_t)(r0 + ty) * n + c]) : MT::zero();
+    sB[ty][tx] = (a0 + ty < k && c < n) ? MT::load(cconj(Bn[(size_t)(a0 + ty) * n + c])) : MT::zero();
     __syncthreads();
 #pragma unroll 4
-    for (int kk = 0; kk < kTile; ++kk) cfma(acc, sA[ty][kk], cconj(sB[tx][kk]));
+    for (int kk = 0; kk < kTile; ++kk) MT::fma(acc, sA[ty][kk], sB[tx][kk]);
     __syncthreads();
   }
   const int r = r0 + ty, a = a0 + tx;
   if (r < m && a < k) {
     const R inv = R(rep->inv_norm);
-    Bout[(size_t)r * k + a] = cmk<R>(acc.x * inv, acc.y * inv);
+    const C v = MT::value(acc);
+    Bout[(size_t)r * k + a] = cmk<R>(v.x * inv, v.y * inv);
   }
 }
 

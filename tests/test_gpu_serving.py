@@ -57,9 +57,19 @@ def test_results_same_alone_and_in_the_mix(budget):
         assert status[0] == 0
         assert got[t][0] == alone[0]
         assert got[t][1] > 0
-    tmpl, c, ham, H, bits, chi = frags[0]
-    f, theta, t = reqs[0]
-    assert abs(got[t][0] - om.vqe_energy(tmpl, theta, bits, ham, chi_max=chi, eps_rel=1e-12)) <= 1e-10
+    # the first request of every untruncated fragment (chi_max >= 2^(n/2))
+    # against the oracle; where chi_max truncates, the spin-degenerate pairs
+    # of these states can straddle the cut, and which member is kept is a
+    # rounding decision (two exact runs then differ by about the discarded
+    # weight), so those fragments are checked alone-vs-mix only
+    checked = 0
+    for f, theta, t in reqs[:len(frags)]:
+        tmpl, c, ham, H, bits, chi = frags[f]
+        if chi < 2 ** (tmpl.n_qubits // 2):
+            continue
+        assert abs(got[t][0] - om.vqe_energy(tmpl, theta, bits, ham, chi_max=chi, eps_rel=1e-12)) <= 1e-10
+        checked += 1
+    assert checked == 2
     srv.close()
 
 
