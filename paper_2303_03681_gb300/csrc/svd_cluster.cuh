@@ -300,45 +300,6 @@ __device__ __forceinline__ void orth_pair(cplx<S>* vi, cplx<S>* vj, int m, int l
   }
 }
 
-// Double-float form of orth_pair (columns of float4 = (re_h, re_l, im_h,
-// im_l)): e = v_i^H v_j summed with exact heads (GramAcc) and in
-// double-float across the warp, then the same symmetric update in
-// double-float arithmetic.
-__device__ __forceinline__ void ff_orth_pair(float4* vi, float4* vj, int m, int len, int lane) {
-  GramAcc ar, ai;
-  for (int r = m + lane; r < len; r += 32) {
-    const float4 x = vi[r], y = vj[r];
-    const ff xr = re_of(x), xi = im_of(x), yr = re_of(y), yi = im_of(y);
-    ar.add(xr, yr);
-    ar.add(xi, yi);
-    ai.add(xr, yi);
-    ai.add(ff_neg(xi), yr);
-  }
-  ff gr = ar.value(), gi = ai.value(), d0 = ff_make(0.f, 0.f), d1 = d0;
-  ff_warp_sum4(gr, gi, d0, d1);
-  gr = ff_make(0.5f * gr.h, 0.5f * gr.l);  // exact halving
-  gi = ff_make(0.5f * gi.h, 0.5f * gi.l);
-  for (int r = m + lane; r < len; r += 32) {
-    const float4 x = vi[r], y = vj[r];
-    const ff xr = re_of(x), xi = im_of(x), yr = re_of(y), yi = im_of(y);
-    // x - conj(g) y and y - g x
-    const ff nxr = ff_sub(xr, ff_add(ff_mul(gr, yr), ff_mul(gi, yi)));
-    const ff nxi = ff_sub(xi, ff_sub(ff_mul(gr, yi), ff_mul(gi, yr)));
-    const ff nyr = ff_sub(yr, ff_sub(ff_mul(gr, xr), ff_mul(gi, xi)));
-    const ff nyi = ff_sub(yi, ff_add(ff_mul(gr, xi), ff_mul(gi, xr)));
-    vi[r] = cff(nxr, nxi);
-    vj[r] = cff(nyr, nyi);
-  }
-}
-
-template <typename T, bool kDF>
-__device__ __forceinline__ void orth_step(cplx<T>* x, cplx<T>* y, int m, int len, int lane) {
-  if constexpr (kDF)
-    ff_orth_pair(reinterpret_cast<float4*>(x), reinterpret_cast<float4*>(y), m, len, lane);
-  else
-    orth_pair<T>(x, y, m, len, lane);
-}
-
 // Cluster-uniform sizes of one SVD.
 struct ClusterGeom {
   int Pl, me;   // CTAs launched, this CTA's rank
@@ -410,7 +371,7 @@ __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColSto
                               bool& converged, const cg::cluster_group& cluster, int* s_flag_in, int* s_any) {
   using C = cplx<T>;
   using E = std::conditional_t<kDF, float4, C>;  // a stored entry
-  static_assert(!kDF || sizeof(float4) == sizeof(C), "double-float columns replace complex128 ones");
+  static_assert(!kDF || (sizeof(float4) == sizeof(C) && kOp == 0), "double-float columns replace complex128 ones");
   // In the cross rounds, when every warp has one top-slot column, warp w
   // keeps it in registers for the b rotations it takes part in; only the
   // bottom-slot columns are re-read, so one barrier per sub-round orders
@@ -499,7 +460,7 @@ __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColSto
                 rotated |= r;
               }
             } else
-              orth_step<T, kDF>(x, y, g.m, g.len, g.wl);
+              orth_pair<T>(x, y, g.m, g.len, g.wl);
           }
           __syncthreads();
         }
@@ -551,7 +512,7 @@ __device__ __forceinline__ int cluster_sweeps(const ClusterGeom& g, const ColSto
                   rotated |= r;
                 }
               } else
-                orth_step<T, kDF>(x, y, g.m, g.len, g.wl);
+                orth_pair<T>(x, y, g.m, g.len, g.wl);
             }
           }
           __syncthreads();
@@ -740,63 +701,32 @@ __device__ __forceinline__ void svd_cluster_body(const ClusterGeom& g, const cg:
                                                p.chi_max, nrm2, tail, flags, conv32, cluster, s_flag_in, s_any);
     used = used32;
     t_lo = clock64();
-    // FP64 columns: V promoted (A follows from the theta below); the
-    // double-float form holds V as double-float values (exact: (v, 0))
+    // FP64 columns: V promoted (A follows from the theta below)
     cur = kGlobal ? 0 : 1;
     for (int slot = 0; slot < 2 && g.member; ++slot)
       for (size_t t = threadIdx.x; t < (size_t)b * ncols; t += nt) {
         const int c = (int)(t / ncols), r = m + (int)(t % ncols);
         const cplx<float> v = cs32.col(cur32, slot, c, 0)[r];
-        if constexpr (kDF)
-          reinterpret_cast<float4*>(cs.col(cur, slot, c, 0))[r] = make_float4(v.x, 0.f, v.y, 0.f);
-        else
-          cs.col(cur, slot, c, 0)[r] = cmk<S>(S(v.x), S(v.y));
+        cs.col(cur, slot, c, 0)[r] = cmk<S>(S(v.x), S(v.y));
       }
     // every CTA has read its FP32 columns before the first hand-over may
     // overwrite them (in shared memory they share a buffer with FP64 ones)
     cluster.sync();
     // two first-order passes: E ~ 1e-6 -> E^2 -> E^4 (one pass left V
-    // unitary only to ~1e-10 after long FP32 phases); in double-float on
-    // the FP32 units for the double-float form
+    // unitary only to ~1e-10 after long FP32 phases)
     for (int pass = 0; pass < 2; ++pass) {
       bool dummy;
-      cluster_sweeps<S, 1, kGlobal, kDF>(g, cs, cur, 1, S(0), S(0), S(0), 0.0, 0, nrm2, tail, flags, dummy, cluster,
-                                         s_flag_in, s_any);
+      cluster_sweeps<S, 1, kGlobal>(g, cs, cur, 1, S(0), S(0), S(0), 0.0, 0, nrm2, tail, flags, dummy, cluster,
+                                    s_flag_in, s_any);
       // the diagonal of the first-order step: |v|^2 -> 1
       for (int c = g.wp; g.member && c < 2 * b; c += g.nw) {
         C* v = cs.col(cur, c / b, c % b, 0);
-        if constexpr (kDF) {
-          float4* vf = reinterpret_cast<float4*>(v);
-          GramAcc na;
-          for (int r = m + g.wl; r < len; r += 32) {
-            const ff vr = re_of(vf[r]), vi = im_of(vf[r]);
-            na.add(vr, vr);
-            na.add(vi, vi);
-          }
-          ff n2 = na.value(), z0 = ff_make(0.f, 0.f), z1 = z0, z2 = z0;
-          ff_warp_sum4(n2, z0, z1, z2);
-          const ff f = ff_sub(ff_make(1.5f, 0.f), ff_make(0.5f * n2.h, 0.5f * n2.l));
-          if (n2.h > 0.f)
-            for (int r = m + g.wl; r < len; r += 32)
-              vf[r] = cff(ff_mul(f, re_of(vf[r])), ff_mul(f, im_of(vf[r])));
-        } else {
-          S n2 = 0;
-          for (int r = m + g.wl; r < len; r += 32) n2 = fma(v[r].x, v[r].x, fma(v[r].y, v[r].y, n2));
-          n2 = warp_sum(n2);
-          const S f = S(1.5) - S(0.5) * n2;
-          if (n2 > S(0))
-            for (int r = m + g.wl; r < len; r += 32) v[r] = cmk<S>(f * v[r].x, f * v[r].y);
-        }
-      }
-      __syncthreads();
-    }
-    if constexpr (kDF) {
-      // V back to FP64 for the rebuild below (once per entry)
-      for (size_t t = threadIdx.x; g.member && t < (size_t)2 * b * ncols; t += nt) {
-        C* col = cs.col(cur, (int)(t / ((size_t)b * ncols)), (int)((t / ncols) % b), 0);
-        const int r = m + (int)(t % ncols);
-        const double2 z = cff_to_double2(reinterpret_cast<const float4*>(col)[r]);
-        col[r] = cmk<S>(S(z.x), S(z.y));
+        S n2 = 0;
+        for (int r = m + g.wl; r < len; r += 32) n2 = fma(v[r].x, v[r].x, fma(v[r].y, v[r].y, n2));
+        n2 = warp_sum(n2);
+        const S f = S(1.5) - S(0.5) * n2;
+        if (n2 > S(0))
+          for (int r = m + g.wl; r < len; r += 32) v[r] = cmk<S>(f * v[r].x, f * v[r].y);
       }
       __syncthreads();
     }
