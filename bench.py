@@ -781,7 +781,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-oracle-check", action="store_true",
                     help="skip the extra evaluation at the stored oracle energy's reference angles")
-    ap.add_argument("--batch", type=int, default=16, help="concurrent evaluations per step")
+    ap.add_argument("--batch", type=int, default=32, help="concurrent evaluations per step")
     ap.add_argument("--tensor-cores", type=int, choices=[0, 1], default=1,
                     help="complex64 environment contractions on tcgen05 (1) or CUDA cores (0)")
     ap.add_argument("--contraction-chi", type=int, default=512,
