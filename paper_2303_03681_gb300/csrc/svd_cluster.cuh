@@ -22,16 +22,17 @@
 // stacked columns do not fit the shared memory they stay in a global
 // workspace, and a round only renames the positions.
 //
-// FP64 accuracy at FP32 speed (complex64 states).  This part runs FP64 at
-// 2 FMA/clk/SM, so an all-FP64 Jacobi of a 100-column theta takes tens of
-// milliseconds.  The mixed form runs the sweeps in FP32 to FP32 convergence
-// (V32 accumulated as usual), re-orthonormalises V32 in FP64 with one
-// pairwise first-order step v_i <- v_i - 1/2 sum_j (v_j^H v_i) v_j (the
-// symmetric update V (I - E / 2), E = V^H V - I, which leaves ||E||^2),
-// rebuilds A = C~ V in FP64 from the theta, and finishes with FP64 sweeps,
+// FP64 accuracy at FP32 speed.  This part runs FP64 at 2 FMA/clk/SM, so an
+// all-FP64 Jacobi of a 100-column theta takes tens of milliseconds.  The
+// mixed form runs the sweeps in FP32 to FP32 convergence (V32 accumulated as
+// usual), re-orthonormalises V32 in FP64 with two pairwise first-order
+// passes v_i <- v_i - 1/2 sum_j (v_j^H v_i) v_j (the symmetric update
+// V (I - E / 2), E = V^H V - I, which leaves ||E||^2), rebuilds A = C~ V in
+// FP64 from the theta, converts the stacked columns to double-float
+// (dfloat.cuh) and finishes with double-float sweeps on the FP32 units,
 // which start near convergence and converge quadratically.  The singular
-// values, the truncation and B~_{q+1} then come from FP64 columns exactly as
-// in the all-FP64 form.
+// values, the truncation and B~_{q+1} then come from columns accurate to
+// about 2^-46 (the all-FP64 form, svd_fp64 = 2, sweeps in FP64 throughout).
 #pragma once
 
 #include <cooperative_groups.h>
