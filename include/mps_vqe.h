@@ -84,9 +84,9 @@ typedef struct {
   int32_t svd_fp64;       /* 0: Jacobi SVD in the storage precision;
                              1: FP64-accurate Jacobi SVD (thetas whose column capacity is 32 or
                                 more: FP32 sweeps to FP32 convergence, two FP64
-                                re-orthonormalisation passes of V, A = C~ V rebuilt in FP64, FP64
-                                sweeps to the FP64 stopping rule; smaller thetas: every sweep in
-                                FP64);
+                                re-orthonormalisation passes of V, A = C~ V rebuilt in FP64,
+                                double-float sweeps on the FP32 units to a stopping rule at unit
+                                roundoff 2^-46; smaller thetas: every sweep in FP64);
                              2: every Jacobi sweep in FP64 */
   int32_t svd_max_sweeps; /* Jacobi sweep cap; 0 selects 60 */
   double svd_tol;         /* rotate a pair while |b_ij| > tol sqrt(b_ii b_jj); 0: default */
